@@ -1,0 +1,48 @@
+"""Write the FP64 oracle's reconstructions of the seeded workloads.
+
+Calls only ``oracle`` (and ``synth`` for the seeded inputs).  Output:
+``tests/golden/admm_<name>.npz`` holding the final image ``x``, the objective
+and relative-change histories, and fingerprints of the k-space input (its
+L2 norm and a few samples) so that a consumer can confirm it regenerated the
+same measurement.
+
+    python tests/golden/make_golden.py small medium
+"""
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+CONFIGS = {"small": synth.config_small, "medium": synth.config_medium}
+SAMPLE_IDX = np.array([0, 1, 17, 1000, 4093, 16383, 123456, 196607])
+
+
+def fingerprint(d):
+    flat = d.reshape(-1)
+    idx = SAMPLE_IDX[SAMPLE_IDX < flat.size]
+    return float(np.linalg.norm(flat.astype(np.complex128))), idx, flat[idx]
+
+
+def main(names):
+    for name in names:
+        p = CONFIGS[name]()
+        t0 = time.time()
+        d = oracle.measurements(p)
+        out = oracle.admm(p.traj, p.maps, d, p.lam, p.beta, p.admm_iters, p.cg_iters)
+        norm, idx, samples = fingerprint(d)
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"admm_{p.name}.npz")
+        np.savez_compressed(path, x=out["x"], objective=out["objective"], alpha=out["alpha"],
+                            d_norm=norm, d_idx=idx, d_samples=samples,
+                            lam=p.lam, beta=p.beta, admm_iters=p.admm_iters, cg_iters=p.cg_iters)
+        print(f"{p.name}: {time.time() - t0:.1f} s with {oracle.get_threads()} threads -> {path}")
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or ["small"])

@@ -1,0 +1,316 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: the FFT on a
+Cartesian grid, closed-form continuous Fourier transforms, operator identities,
+dense linear algebra built from unit-vector probes, and worked values of Eq. 9.
+A plausible slip (a flipped sign in the exponent, a shifted pixel origin, a
+missing coil conjugate, a wrong boundary in Theta, a dropped CG term) fails at
+least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+def _cplx(rng, shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def _unit_maps(rng, nx, ny, nc):
+    """Coil maps with sum_c |S_c|^2 = 1 to double precision."""
+    m = synth.coil_maps(rng, nx, ny, nc).astype(np.complex128)
+    return m / np.sqrt(np.sum(np.abs(m) ** 2, axis=0))[None]
+
+
+# --------------------------------------------------------------------------
+# Eq. 1 on a Cartesian grid equals the centred FFT
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,ny", [(16, 16), (12, 10), (9, 7)])
+def test_forward_equals_centred_fft_on_cartesian_grid(nx, ny):
+    rng = _rng(1)
+    x = _cplx(rng, (nx, ny))
+    maps = _cplx(rng, (3, nx, ny))
+    traj = synth.cartesian_trajectory(nx, ny, np.float64)
+    d = oracle.forward(traj, x, maps)
+    for c in range(3):
+        ref = np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(maps[c] * x)))
+        got = d[c].reshape(nx, ny)
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_normal_operator_is_scaled_identity_on_full_cartesian_grid():
+    # sum_c |S_c|^2 = 1 and all nx*ny grid frequencies: F^H F = nx*ny * I.
+    nx, ny = 12, 8
+    rng = _rng(2)
+    maps = _unit_maps(rng, nx, ny, 4)
+    x = _cplx(rng, (nx, ny))
+    traj = synth.cartesian_trajectory(nx, ny, np.float64)
+    out = oracle.normal(traj, maps, 0.0, x)
+    assert np.abs(out - nx * ny * x).max() <= 1e-11 * nx * ny * np.abs(x).max()
+
+
+# --------------------------------------------------------------------------
+# Eq. 1 against closed-form continuous transforms
+# --------------------------------------------------------------------------
+def test_forward_matches_gaussian_blob_transform_exactly():
+    # Poisson summation: sum_n g(n) e^{-i2pi k.n} = sum_m G(k+m), with G the
+    # continuous transform of the sampled Gaussian; the blob sits well inside
+    # the grid so truncation and the m outside {-1,0,1}^2 are below 1e-19.
+    n = 64
+    cov = np.array([[7.5, 1.2], [1.2, 6.3]])
+    cen = np.array([1.3, -2.1])
+    X = synth.pixel_coords(n)
+    XX, YY = np.meshgrid(X, X, indexing="ij")
+    r = np.stack([XX - cen[0], YY - cen[1]], axis=-1)
+    inv = np.linalg.inv(cov)
+    img = np.exp(-0.5 * np.einsum("...i,ij,...j->...", r, inv, r))
+    rng = _rng(3)
+    k = rng.uniform(-0.5, 0.5, (300, 2)).astype(np.float32).astype(np.float64)
+    d = oracle.forward(k, img, np.ones((1, n, n)))[0]
+    ref = np.zeros(len(k), np.complex128)
+    amp = 2.0 * math.pi * math.sqrt(np.linalg.det(cov))
+    for mx in (-1, 0, 1):
+        for my in (-1, 0, 1):
+            q = k + np.array([mx, my])
+            ref += amp * np.exp(-2 * math.pi ** 2 * np.einsum("ki,ij,kj->k", q, cov, q)) \
+                * np.exp(-2j * math.pi * (q @ cen))
+    assert np.abs(d - ref).max() <= 1e-11 * amp
+
+
+def test_forward_matches_ellipse_bessel_transform():
+    # Uniform ellipse: F(k) = a b J1(2 pi rho)/rho e^{-i 2 pi k.c}; the 8x8
+    # supersampled raster approximates the indicator, so the pin is loose.
+    from scipy.special import j1
+    n = 64
+    e = synth.Ellipse(3.3, -5.2, 14.0, 9.0, 0.6, 1.0)
+    img = synth.rasterize([e], n, n, ss=8)
+    rng = _rng(4)
+    k = rng.uniform(-0.25, 0.25, (200, 2)).astype(np.float32).astype(np.float64)
+    d = oracle.forward(k, img, np.ones((1, n, n)))[0]
+    u = np.array([math.cos(e.angle), math.sin(e.angle)])
+    v = np.array([-math.sin(e.angle), math.cos(e.angle)])
+    rho = np.sqrt((e.a * (k @ u)) ** 2 + (e.b * (k @ v)) ** 2)
+    ref = e.a * e.b * j1(2 * math.pi * rho) / rho * np.exp(-2j * math.pi * (k @ np.array([e.cx, e.cy])))
+    area = math.pi * e.a * e.b
+    assert np.abs(d - ref).max() <= 1e-2 * area
+    # the conjugate (wrong exponent sign) is far off
+    assert np.abs(np.conj(d) - ref).max() > 0.3 * area
+
+
+# --------------------------------------------------------------------------
+# Adjoint identities and dense brute force at 8x8
+# --------------------------------------------------------------------------
+def _small_problem(seed=5, n=8, nc=3, spokes=6, readout=16):
+    rng = _rng(seed)
+    maps = synth.coil_maps(rng, n, n, nc).astype(np.complex128)
+    traj = synth.radial_trajectory(spokes, readout, golden=True)
+    return rng, maps, traj
+
+
+def _dense(op, shape_in):
+    size = int(np.prod(shape_in))
+    cols = []
+    for q in range(size):
+        e = np.zeros(size, np.complex128)
+        e[q] = 1.0
+        cols.append(np.asarray(op(e.reshape(shape_in))).reshape(-1))
+    return np.stack(cols, axis=1)
+
+
+def test_adjoint_identity_radial():
+    rng, maps, traj = _small_problem(n=24, nc=4, spokes=10, readout=48)
+    x = _cplx(rng, (24, 24))
+    y = _cplx(rng, (4, traj.shape[0]))
+    lhs = np.vdot(oracle.forward(traj, x, maps), y)
+    rhs = np.vdot(x, oracle.adjoint(traj, y, maps))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_brute_force_8x8_operators():
+    rng, maps, traj = _small_problem()
+    n = 8
+    E = _dense(lambda v: oracle.forward(traj, v, maps), (n, n))
+    # the dense matrix built from unit probes is the direct sum of Eq. 1
+    xs = synth.pixel_coords(n)
+    XX, YY = np.meshgrid(xs, xs, indexing="ij")
+    kt = traj.astype(np.float64)
+    phase = np.exp(-2j * np.pi * (np.outer(kt[:, 0], XX.reshape(-1)) + np.outer(kt[:, 1], YY.reshape(-1))))
+    E_ref = np.concatenate([phase * maps[c].reshape(1, -1) for c in range(maps.shape[0])], axis=0)
+    assert np.abs(E - E_ref).max() <= 1e-12
+    # adjoint = conjugate transpose
+    y = _cplx(rng, (maps.shape[0], traj.shape[0]))
+    assert np.abs(oracle.adjoint(traj, y, maps).reshape(-1) - E.conj().T @ y.reshape(-1)).max() <= 1e-11
+    # Theta^H is the transpose of Theta
+    D = _dense(oracle.tv_forward, (n, n))
+    DH = _dense(oracle.tv_adjoint, (2, n, n))
+    assert np.array_equal(DH, D.conj().T)
+    # normal operator
+    beta = 0.7
+    A = _dense(lambda v: oracle.normal(traj, maps, beta, v), (n, n))
+    assert np.abs(A - (E.conj().T @ E + 0.5 * beta * D.conj().T @ D)).max() <= 1e-10
+
+
+def test_theta_structure():
+    n = 6
+    # one axis: D^T D is tridiagonal with diagonal (1, 2, ..., 2), off-diagonals -1
+    D = _dense(oracle.tv_forward, (n, n)).real
+    Dx = D[: n * n]
+    DtD = Dx.T @ Dx
+    ref1 = np.diag([1.0] + [2.0] * (n - 1)) - np.diag(np.ones(n - 1), 1) - np.diag(np.ones(n - 1), -1)
+    assert np.array_equal(DtD, np.kron(ref1, np.eye(n)))
+    # a constant image has zero differences except the last row/column (-c)
+    c = 2.0 - 1.0j
+    g = oracle.tv_forward(np.full((n, n), c))
+    assert np.all(g[0, :-1, :] == 0) and np.all(g[0, -1, :] == -c)
+    assert np.all(g[1, :, :-1] == 0) and np.all(g[1, :, -1] == -c)
+    # a ramp along x has unit differences inside
+    ramp = np.arange(n)[:, None] * np.ones((1, n))
+    g = oracle.tv_forward(ramp)
+    assert np.all(g[0, :-1] == 1.0) and np.all(g[1, :, :-1] == 0.0)
+
+
+# --------------------------------------------------------------------------
+# Soft threshold (Eq. 8-9)
+# --------------------------------------------------------------------------
+def test_shrink_reproduces_eq9_worked_values():
+    rows = np.loadtxt(os.path.join(GOLDEN, "eq9_soft_threshold.txt"), comments="#")
+    for a, lam, beta, expected in rows:
+        got = oracle.shrink(np.array([a + 0j]), lam / beta)[0]
+        assert got.imag == 0.0
+        assert abs(got.real - expected) <= 1e-15 * max(1.0, abs(expected))
+
+
+def test_shrink_is_the_prox_of_the_modulus():
+    # argmin_mu t|mu| + 1/2 |mu - a|^2, found by brute force on a fine grid
+    rng = _rng(6)
+    for _ in range(6):
+        a = complex(*rng.uniform(-2, 2, 2))
+        t = float(rng.uniform(0.1, 1.5))
+        g = np.linspace(-2.5, 2.5, 1001)
+        MR, MI = np.meshgrid(g, g, indexing="ij")
+        mu = MR + 1j * MI
+        cost = t * np.abs(mu) + 0.5 * np.abs(mu - a) ** 2
+        q = np.unravel_index(np.argmin(cost), cost.shape)
+        got = oracle.shrink(np.array([a]), t)[0]
+        assert abs(got - mu[q]) <= 2 * (g[1] - g[0])
+
+
+# --------------------------------------------------------------------------
+# Conjugate gradient (Alg. 2)
+# --------------------------------------------------------------------------
+def test_cg_matches_dense_solve_and_decreases_energy_error():
+    rng, maps, traj = _small_problem(seed=7)
+    n, beta = 8, 1.0
+    A = _dense(lambda v: oracle.normal(traj, maps, beta, v), (n, n))
+    b = _cplx(rng, (n, n))
+    x_star = np.linalg.solve(A, b.reshape(-1))
+    x0 = np.zeros((n, n), np.complex128)
+    # first step by hand: x1 = alpha r0 with alpha = |r0|^2 / <r0, A r0>
+    x1, steps, _ = oracle.cg(traj, maps, beta, b, x0, 1)
+    r0 = b.reshape(-1)
+    alpha = np.vdot(r0, r0).real / np.vdot(r0, A @ r0).real
+    assert steps == 1 and np.abs(x1.reshape(-1) - alpha * r0).max() <= 1e-12 * np.abs(alpha * r0).max()
+    # A-norm error is non-increasing along the iterations
+    errs = []
+    for k in range(0, 30, 3):
+        xk, _, _ = oracle.cg(traj, maps, beta, b, x0, k)
+        e = xk.reshape(-1) - x_star
+        errs.append(np.vdot(e, A @ e).real)
+    assert all(errs[i + 1] <= errs[i] * (1 + 1e-9) for i in range(len(errs) - 1))
+    # converges to the dense solution
+    xk, _, tau = oracle.cg(traj, maps, beta, b, x0, 400)
+    assert np.linalg.norm(xk.reshape(-1) - x_star) <= 1e-8 * np.linalg.norm(x_star)
+    # warm start from the solution: already converged
+    xs, steps, _ = oracle.cg(traj, maps, beta, b, x_star.reshape(n, n), 5, atol=1e-6)
+    assert steps == 0
+
+
+def test_cg_atol_stops_early():
+    rng, maps, traj = _small_problem(seed=8)
+    b = _cplx(rng, (8, 8))
+    x, steps, tau = oracle.cg(traj, maps, 1.0, b, np.zeros((8, 8)), 500, atol=1e-3)
+    assert steps < 500 and tau[-1] <= 1e-6 and tau[-2] > 1e-6
+
+
+# --------------------------------------------------------------------------
+# ADMM (Alg. 4, Eq. 6-12)
+# --------------------------------------------------------------------------
+def test_admm_lambda_zero_converges_to_least_squares():
+    rng, maps, traj = _small_problem(seed=9, nc=4, spokes=8, readout=16)
+    n = 8
+    E = _dense(lambda v: oracle.forward(traj, v, maps), (n, n))
+    d = _cplx(rng, (maps.shape[0], traj.shape[0]))
+    x_ls = np.linalg.lstsq(E, d.reshape(-1), rcond=None)[0]
+    out = oracle.admm(traj, maps, d, lam=0.0, beta=0.05, admm_iters=60, cg_iters=64)
+    assert np.linalg.norm(out["x"].reshape(-1) - x_ls) <= 1e-6 * np.linalg.norm(x_ls)
+
+
+def test_admm_full_cartesian_one_step_is_centred_ifft_coil_combine():
+    nx, ny = 12, 8
+    rng = _rng(10)
+    maps = _unit_maps(rng, nx, ny, 3)
+    traj = synth.cartesian_trajectory(nx, ny, np.float64)
+    d = _cplx(rng, (3, nx * ny))
+    out = oracle.admm(traj, maps, d, lam=0.0, beta=1e-12, admm_iters=1, cg_iters=3)
+    ref = np.zeros((nx, ny), np.complex128)
+    for c in range(3):
+        ref += np.conj(maps[c]) * np.fft.fftshift(np.fft.ifft2(np.fft.ifftshift(d[c].reshape(nx, ny))))
+    assert np.abs(out["x"] - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_admm_kkt_conditions_at_convergence():
+    rng, maps, traj = _small_problem(seed=11, nc=4, spokes=8, readout=16)
+    n = 8
+    x_true = synth.rasterize(synth.random_ellipses(rng, n, n, 3), n, n).astype(np.complex128)
+    d = oracle.forward(traj, x_true, maps) + 0.05 * _cplx(rng, (4, traj.shape[0]))
+    lam, beta = 2.0, 200.0
+    out = oracle.admm(traj, maps, d, lam, beta, admm_iters=400, cg_iters=64, want_state=True)
+    x, mu, eta = out["x"], out["mu"], out["eta"]
+    Dx = oracle.tv_forward(x)
+    # primal feasibility: Theta x = mu
+    assert np.linalg.norm(Dx - mu) <= 1e-6 * np.linalg.norm(Dx)
+    # stationarity in x: 2 F^H (F x - d) + beta Theta^H eta = 0
+    g = 2 * oracle.adjoint(traj, oracle.forward(traj, x, maps) - d, maps) + beta * oracle.tv_adjoint(eta)
+    assert np.linalg.norm(g) <= 1e-5 * np.linalg.norm(2 * oracle.adjoint(traj, d, maps))
+    # dual feasibility of the l1 term: |beta eta| <= lambda, equality where mu != 0
+    assert np.all(np.abs(beta * eta) <= lam * (1 + 1e-5))
+    nz = np.abs(mu) > 1e-8
+    assert np.allclose(beta * eta[nz], lam * mu[nz] / np.abs(mu[nz]), atol=1e-4 * lam)
+
+
+def test_admm_objective_decreases_on_small_config():
+    p = synth.config_small()
+    d = oracle.measurements(p)
+    out = oracle.admm(p.traj, p.maps, d, p.lam, p.beta, p.admm_iters, p.cg_iters)
+    f = out["objective"]
+    assert out["steps"] == p.admm_iters
+    assert np.all(np.diff(f) <= 1e-6 * np.abs(f[:-1]))
+    # the reconstruction is a reasonable image of the phantom
+    err = np.linalg.norm(out["x"] - p.image_true) / np.linalg.norm(p.image_true)
+    assert err < 0.2
+
+
+def test_admm_table1_parameters_stop_on_tolerances():
+    with open(os.path.join(GOLDEN, "table1_admm_params.json")) as fh:
+        t1 = json.load(fh)
+    p = synth.config_small()
+    d = oracle.measurements(p)
+    out = oracle.admm(p.traj, p.maps, d, t1["lambda"], t1["beta"], t1["admm_max_iterations"],
+                      t1["cg_max_iterations"], rtol=t1["admm_rtol"], atol=t1["cg_atol"])
+    assert 1 <= out["steps"] <= t1["admm_max_iterations"]
+    a = out["alpha"]
+    # every step but the last saw alpha above rtol^2 (Alg. 4 loop condition)
+    assert np.all(a[:-1] > t1["admm_rtol"] ** 2)
+    assert out["steps"] == t1["admm_max_iterations"] or a[-1] <= t1["admm_rtol"] ** 2
