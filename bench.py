@@ -1,0 +1,353 @@
+"""Benchmark of the ADMM reconstruction hot path on GB300.
+
+One step = one complete reconstruction of the N=128 workload (12 coils, 64
+golden-angle spokes x 256 readout samples, 30 ADMM x 8 CG iterations,
+lambda=1e-3, beta=1): DFT-factor generation for the step's trajectory
+(Alg. 1) followed by Alg. 4 with Alg. 2 inside, in the BF16x3 tensor-core
+form.  The plain FP32 form is timed beside it on the same GPU.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Each rank reconstructs its own problems (independent
+reconstructions: weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "n128_c12_s64x256_admm30x8"
+METRIC = ("ADMM recon/s, N=128 image, 12 coils, 64 golden-angle spokes x 256 samples, 30 ADMM x 8 CG, "
+          "BF16x3 tensor-core NUDFT (FP32 form beside)")
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            m = json.load(fh)
+        return m, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def problem():
+    return synth.config_medium()
+
+
+def normal_ops_per_recon(p):
+    # A x0 plus one A d per CG step in every outer step, plus F^H d once (half an op)
+    return p.admm_iters * (p.cg_iters + 1) + 0.5
+
+
+def useful_flops_per_product(p):
+    # complex MACs of one separable DFT product, 8 real flops each
+    return 8.0 * p.nk * p.nx * p.ny * p.nc
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [q.strip() for q in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        loaded = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import paper_2006_14080_gb300 as mr
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    p = problem()
+    stream = torch.cuda.current_stream()
+    traj = torch.from_numpy(p.traj).to(dev)
+    maps = torch.from_numpy(p.maps).to(dev)
+    ximg = torch.from_numpy(p.image_true).to(dev)
+
+    # measurement: the library's FP32 forward model of the phantom plus the seeded noise
+    with mr.Plan(p.nx, p.ny, p.nc, traj, "fp32") as plan32:
+        d_clean = mr.nudft_forward(plan32, ximg, maps).cpu().numpy()
+    kspace_np = synth.add_noise(d_clean, p.noise, p.noise_level)
+    kspace = torch.from_numpy(kspace_np).to(dev)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed_steps(plan, out, steps, warmup, host=None, plan_timed=False):
+        """Returns (per-step device ms list, launches per step)."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+
+        def one(i_ev=None):
+            if host is not None:
+                # end-to-end: pinned host inputs in, image out, all inside the timed region
+                h_traj, h_k, h_maps, h_out, d_traj, d_k, d_maps = host
+                d_traj.copy_(h_traj, non_blocking=True)
+                d_k.copy_(h_k, non_blocking=True)
+                d_maps.copy_(h_maps, non_blocking=True)
+                plan.set_trajectory(d_traj)
+                mr.admm_reconstruct(plan, d_k, d_maps, p.lam, p.beta, p.admm_iters, p.cg_iters, out=out)
+                h_out.copy_(out, non_blocking=True)
+            else:
+                plan.set_trajectory(traj)
+                mr.admm_reconstruct(plan, kspace, maps, p.lam, p.beta, p.admm_iters, p.cg_iters, out=out)
+
+        for _ in range(warmup):
+            one()
+        barrier()
+        if plan_timed:
+            plan.read_timing()  # forget the warm-up launches
+        l0 = plan.launch_count()
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            one()
+            ev[i][1].record(stream)
+        barrier()
+        launches = plan.launch_count() - l0
+        return [a.elapsed_time(b) for a, b in ev], launches
+
+    results = {}
+    out = torch.empty((p.nx, p.ny), dtype=torch.complex64, device=dev)
+    with mr.Plan(p.nx, p.ny, p.nc, traj, "bf16x3") as plan:
+        gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]) \
+            if os.environ.get("CUDA_VISIBLE_DEVICES") else local_rank
+        with ClockSampler(gpu_index) as clk:
+            plan.set_timing(True)
+            times, launches = timed_steps(plan, out, args.steps, args.warmup, plan_timed=True)
+            timing = plan.read_timing()
+            plan.set_timing(False)
+        results["bf16x3"] = (times, launches, timing, clk.summary())
+        x_bf16 = out.cpu().numpy()
+
+        # end to end through the same API with pinned host buffers
+        host = (torch.from_numpy(p.traj).pin_memory(), torch.from_numpy(kspace_np).pin_memory(),
+                torch.from_numpy(p.maps).pin_memory(),
+                torch.empty((p.nx, p.ny), dtype=torch.complex64).pin_memory(),
+                torch.empty_like(traj), torch.empty_like(kspace), torch.empty_like(maps))
+        e2e_times, _ = timed_steps(plan, out, args.steps, max(1, args.warmup // 2), host=host)
+        h2d = sum(t.numel() * t.element_size() for t in host[:3])
+        d2h = host[3].numel() * host[3].element_size()
+
+    fp32_steps = max(2, min(args.steps, 3))
+    with mr.Plan(p.nx, p.ny, p.nc, traj, "fp32") as plan32:
+        plan32.set_timing(True)
+        t32, l32 = timed_steps(plan32, out, fp32_steps, 1, plan_timed=True)
+        timing32 = plan32.read_timing()
+        x_fp32 = out.cpu().numpy()
+
+    # ---------------------------------------------------------------- report
+    times, launches, timing, clocks = results["bf16x3"]
+    total_ms = max_over_ranks(sum(times))
+    e2e_ms = max_over_ranks(sum(e2e_times))
+    t32_ms = max_over_ranks(sum(t32))
+    if rank != 0:
+        return None
+    recon_s = world * args.steps / (total_ms / 1e3)
+    flops_prod = useful_flops_per_product(p)
+    pk, pk_kind = peaks()
+    # dominant kernel: the product kernel with the larger share of the timed region
+    fwd_avg = timing["fwd_ms"] / max(1, timing["fwd_launches"])
+    adj_avg = timing["adj_ms"] / max(1, timing["adj_launches"])
+    dom = "adj" if timing["adj_ms"] >= timing["fwd_ms"] else "fwd"
+    dom_avg_ms = adj_avg if dom == "adj" else fwd_avg
+    executed = 3.0 * flops_prod  # hi*hi + hi*lo + lo*hi bf16 tensor products
+    achieved = executed / (dom_avg_ms * 1e-3) / 1e12
+    peak_tf = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    useful_tflops_step = normal_ops_per_recon(p) * 2 * flops_prod / (total_ms / args.steps * 1e-3) / 1e12
+    nrmse_vs_golden = None
+    gpath = os.path.join(ROOT, "tests", "golden", f"admm_{p.name}.npz")
+    if os.path.exists(gpath):
+        xg = np.load(gpath)["x"]
+        nrmse_vs_golden = {
+            "bf16x3": float(np.linalg.norm(x_bf16 - xg) / np.linalg.norm(xg)),
+            "fp32": float(np.linalg.norm(x_fp32 - xg) / np.linalg.norm(xg)),
+        }
+    line = {
+        "metric": METRIC,
+        "value": recon_s,
+        "unit": "recon/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "bf16x3/f32",
+        "data": "synthetic (seeded ellipse phantom, Gaussian coil maps, golden-angle radial, 0.5% noise)",
+        "config": {"workload": WORKLOAD, "nx": p.nx, "ny": p.ny, "coils": p.nc, "spokes": p.spokes,
+                   "readout": p.readout, "admm_iters": p.admm_iters, "cg_iters": p.cg_iters, "lambda": p.lam,
+                   "beta": p.beta, "l2": "flushed (512 MB write) between timed steps",
+                   "step": "factor generation for the step's trajectory + full ADMM reconstruction"},
+        "e2e": {"value": world * args.steps / (e2e_ms / 1e3), "unit": "recon/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": {"bound": "tensor", "kernel": "adj_tc_kernel" if dom == "adj" else "fwd_tc_kernel",
+                     "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf,
+                     "traffic": None,
+                     "note": f"executed bf16 tensor flops (3 products x 8*nk*nx*ny*nc) per launch / mean launch "
+                             f"time ({dom_avg_ms:.4f} ms over {timing[dom + '_launches']} launches), "
+                             f"peak = {pk_kind} sustained bf16"},
+        "nudft": {"fwd_ms_per_launch": fwd_avg, "adj_ms_per_launch": adj_avg,
+                  "fwd_useful_tflops": flops_prod / (fwd_avg * 1e-3) / 1e12,
+                  "adj_useful_tflops": flops_prod / (adj_avg * 1e-3) / 1e12,
+                  "product_share_of_step": (timing["fwd_ms"] + timing["adj_ms"]) / sum(times),
+                  "recon_useful_tflops": useful_tflops_step},
+        "fp32_form": {"value": world * fp32_steps / (t32_ms / 1e3), "unit": "recon/s",
+                      "ms_per_step": t32_ms / fp32_steps, "gpu_launches": l32,
+                      "fwd_ms_per_launch": timing32["fwd_ms"] / max(1, timing32["fwd_launches"]),
+                      "adj_ms_per_launch": timing32["adj_ms"] / max(1, timing32["adj_launches"])},
+        "nrmse_vs_fp64_oracle": nrmse_vs_golden,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+    return line
+
+
+def oracle_sample(p, budget_s):
+    """Time the FP64 oracle's normal operator (Eq. 11) at the workload's full
+    size; one reconstruction needs normal_ops_per_recon() of them."""
+    import oracle
+    rng = np.random.default_rng(7)
+    x = synth.random_complex(rng, (p.nx, p.ny)).astype(np.complex128)
+    oracle.normal(p.traj, p.maps, p.beta, x)  # warm (threads, pages)
+    times = []
+    t_start = time.time()
+    while not times or (time.time() - t_start < budget_s and len(times) < 8):
+        t0 = time.perf_counter()
+        oracle.normal(p.traj, p.maps, p.beta, x)
+        times.append(time.perf_counter() - t0)
+    per_op = statistics.median(times)
+    return per_op, len(times), oracle.get_threads()
+
+
+def cpu_baseline(p, budget_s):
+    per_op, n, threads = oracle_sample(p, budget_s)
+    return {"value": 1.0 / (per_op * normal_ops_per_recon(p)), "unit": "recon/s", "cores": threads,
+            "kind": "oracle",
+            "sample": f"{n} FP64 normal operators (Eq. 11) at the full {WORKLOAD} size, median "
+                      f"{per_op:.2f} s each, scaled by {normal_ops_per_recon(p)} operators per reconstruction"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    p = problem()
+    per_step = []
+    for _ in range(args.warmup):
+        oracle_sample(p, 0.0)
+    for _ in range(args.steps):
+        per_op, _, threads = oracle_sample(p, 0.0)
+        per_step.append(per_op * normal_ops_per_recon(p))
+    total = sum(per_step)
+    value = args.steps / total
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "recon/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": value, "unit": "recon/s", "cores": threads, "kind": "oracle",
+                         "sample": "each step: one FP64 normal operator (Eq. 11) at full size, scaled by "
+                                   f"{normal_ops_per_recon(p)} operators per reconstruction"},
+        "e2e": {"value": value, "unit": "recon/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+    else:
+        line = run_gpu(args, rank, world, local_rank)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

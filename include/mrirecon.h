@@ -1,0 +1,198 @@
+/*
+ * mrirecon -- GB300 (sm_103a) library for TV-regularised multi-coil MRI
+ * reconstruction with ADMM, after Lu et al., "Accelerating MRI Reconstruction
+ * on TPUs" (arXiv 2006.14080).
+ *
+ * The non-uniform DFT of Eq. 1 is evaluated in separable form as dense
+ * complex matrix products:
+ *     y_c = rowsum((A_x (S_c . X)) . A_y),          A_x[k][i] = exp(-i 2 pi kx_k x_i)
+ *     X   = sum_c conj(S_c) . (A_x^H diag(y_c) conj(A_y)),  A_y[k][j] = exp(-i 2 pi ky_k y_j)
+ * with pixel coordinates x_i = i - nx/2, y_j = j - ny/2 (integer division) and
+ * k in cycles/pixel.  The DFT is unnormalised.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Array pointers are DEVICE pointers owned by the caller unless a call says
+ *    otherwise; the library never frees them and never keeps them after the
+ *    call returns.  Arrays must not overlap unless a call allows it.
+ *  - Complex values are interleaved complex64 (mri_c64: re, im floats), C
+ *    row-major:
+ *        image       [nx][ny]      (the first index is the one A_x multiplies)
+ *        coil_maps   [nc][nx][ny]
+ *        kspace      [nc][nk]
+ *        traj        [nk][2] float (kx, ky) in cycles/pixel, nominally [-0.5, 0.5)
+ *        TV fields   [2][nx][ny]   (differences along x, then along y)
+ *  - Every call that takes a stream enqueues its work on that stream and
+ *    returns without synchronising (except where stated).  Deferred device
+ *    failures (a bounded device-side wait that gave up) are reported by
+ *    mri_plan_sync_status().
+ *  - Return value: MRI_OK (0) or a negative MRI_ERR_* code; the calling
+ *    thread's mri_last_error() then describes the failure.  On error no
+ *    output is guaranteed to be written.
+ *  - A plan (mri_plan) owns the DFT factors for one trajectory and all
+ *    workspace; calls on one plan must be serialised by the caller (one
+ *    stream at a time).  Different plans are independent.
+ */
+#ifndef MRIRECON_H
+#define MRIRECON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MRI_API __attribute__((visibility("default")))
+#else
+#define MRI_API
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *mri_stream_t;
+
+typedef struct { float re, im; } mri_c64;
+
+typedef struct mri_plan mri_plan;
+
+/* Status codes. */
+#define MRI_OK               0
+#define MRI_ERR_INVALID     -1  /* null pointer, dimension <= 0, non-finite parameter, bad enum */
+#define MRI_ERR_NOMEM       -2  /* device allocation failed or a memory budget would be exceeded */
+#define MRI_ERR_CUDA        -3  /* a CUDA runtime call failed */
+#define MRI_ERR_TIMEOUT     -4  /* a bounded device-side wait gave up */
+#define MRI_ERR_UNSUPPORTED -5  /* precision / shape combination not available */
+
+/* Arithmetic of the two dense products inside the DFT operators. */
+#define MRI_FP32   0  /* FP32 FFMA on the CUDA cores */
+#define MRI_BF16X3 2  /* tcgen05 BF16 tensor cores, hi+lo split operands, three
+                         products (hi*hi + hi*lo + lo*hi), FP32 accumulation */
+
+/* Text of the last failure on the calling thread ("" if none). */
+MRI_API const char *mri_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+MRI_API int mri_version(void);
+
+/*
+ * Create a plan for an nx x ny image, nc coils and nk samples per coil, and
+ * generate the DFT factors A_x, A_y for traj (device, [nk][2] float) -- the
+ * per-core operator generation of Alg. 1, in separable form.  The phase
+ * k*x is formed and reduced to [-1/2, 1/2] in FP64 before the FP32 sine and
+ * cosine.  traj is read during the call (stream-ordered on `stream`) and not
+ * kept.  precision is MRI_FP32 or MRI_BF16X3.  Allocates device memory (the
+ * factors plus workspace, O(nk*(nx+ny)) + O(nc*nx*ny)); *plan receives the
+ * handle, or NULL on error.
+ */
+MRI_API int mri_plan_create(mri_plan **plan, int nx, int ny, int nk, int nc,
+                            const float *traj, int precision, mri_stream_t stream);
+
+/* Regenerate the factors of an existing plan for a new trajectory of the
+ * same nk (Alg. 1).  No allocation. */
+MRI_API int mri_plan_set_trajectory(mri_plan *plan, const float *traj, mri_stream_t stream);
+
+/* Release a plan and everything it owns.  Synchronises the device first.
+ * NULL is accepted. */
+MRI_API int mri_plan_destroy(mri_plan *plan);
+
+/* Wait for all work on `stream` and report deferred device-side failures of
+ * this plan (MRI_ERR_TIMEOUT when a bounded wait gave up); clears them. */
+MRI_API int mri_plan_sync_status(mri_plan *plan, mri_stream_t stream);
+
+/* Bytes of device memory the plan holds. */
+MRI_API size_t mri_plan_device_bytes(const mri_plan *plan);
+
+/*
+ * Forward operator F of Eq. 1-2:
+ *   kspace[c][k] = sum_{i,j} coil_maps[c][i][j] image[i][j] exp(-i 2 pi (kx_k x_i + ky_k y_j))
+ * image [nx][ny], coil_maps [nc][nx][ny] -> kspace [nc][nk].
+ */
+MRI_API int mri_nudft_forward(mri_plan *plan, const mri_c64 *image, const mri_c64 *coil_maps,
+                              mri_c64 *kspace, mri_stream_t stream);
+
+/*
+ * Adjoint F^H (the inverse-DFT step of Alg. 3 followed by the coil
+ * combination; the paper's cross-core partial-image sum becomes an on-chip
+ * fixed-order reduction over k-space splits):
+ *   image[i][j] = sum_c conj(coil_maps[c][i][j]) sum_k kspace[c][k] exp(+i 2 pi (kx_k x_i + ky_k y_j))
+ * kspace [nc][nk], coil_maps [nc][nx][ny] -> image [nx][ny].
+ */
+MRI_API int mri_nudft_adjoint(mri_plan *plan, const mri_c64 *kspace, const mri_c64 *coil_maps,
+                              mri_c64 *image, mri_stream_t stream);
+
+/*
+ * Normal operator of the x-update, Eq. 11 (linear_op of Alg. 2 / Alg. 3):
+ *   out = F^H F image + (beta/2) Theta^H Theta image
+ * beta = 0 gives F^H F alone.  image and out are [nx][ny] and must differ.
+ */
+MRI_API int mri_normal_op(mri_plan *plan, const mri_c64 *image, const mri_c64 *coil_maps,
+                          float beta, mri_c64 *out, mri_stream_t stream);
+
+/*
+ * Sparsifying transform Theta (first-order finite differences, the conv1d of
+ * Section IV-B, zero past the last pixel):
+ *   grad[0][i][j] = image[i+1][j] - image[i][j],  grad[1][i][j] = image[i][j+1] - image[i][j]
+ * image [nx][ny] -> grad [2][nx][ny].  Needs no plan.
+ */
+MRI_API int mri_tv_forward(int nx, int ny, const mri_c64 *image, mri_c64 *grad, mri_stream_t stream);
+
+/* Theta^H, the exact transpose of mri_tv_forward:
+ *   image[i][j] = grad[0][i-1][j] - grad[0][i][j] + grad[1][i][j-1] - grad[1][i][j]  (grad[.][-1] = 0)
+ * grad [2][nx][ny] -> image [nx][ny]. */
+MRI_API int mri_tv_adjoint(int nx, int ny, const mri_c64 *grad, mri_c64 *image, mri_stream_t stream);
+
+/* Soft threshold of Eq. 8-9 applied to complex values (magnitude shrink):
+ *   out = in * (1 - t/|in|) where |in| > t, else 0.   n elements; in == out allowed. */
+MRI_API int mri_soft_threshold(int n, float t, const mri_c64 *in, mri_c64 *out, mri_stream_t stream);
+
+/* ADMM parameters (Eq. 5-12, Alg. 2 and Alg. 4; the paper's Table I lists one set). */
+typedef struct {
+    float lambda;     /* regularisation weight of Eq. 3 (>= 0) */
+    float beta;       /* augmented-Lagrangian parameter of Eq. 5 (> 0) */
+    int admm_iters;   /* maximum outer iterations (>= 0) */
+    int cg_iters;     /* maximum CG iterations per x-update (>= 0) */
+    double rtol;      /* Alg. 4: stop when ||x'-x||^2/||x'||^2 <= rtol^2 (0: fixed count) */
+    double atol;      /* Alg. 2: stop CG when ||r||^2 <= atol^2 (0: fixed count) */
+} mri_admm_params;
+
+/*
+ * Full reconstruction (Alg. 4): starting from x = 0 and eta = 0, each outer
+ * step computes mu = S_{lambda/beta}(Theta x + eta), b = F^H d +
+ * (beta/2) Theta^H (mu - eta), solves A x' = b by CG warm-started from x
+ * (A = F^H F + (beta/2) Theta^H Theta), then eta += Theta x' - mu.
+ * kspace [nc][nk] and coil_maps [nc][nx][ny] are device inputs; image_out
+ * [nx][ny] receives the final image.  objective_hist and alpha_hist are
+ * nullable DEVICE arrays of admm_iters doubles receiving, after each outer
+ * step, the Eq. 3 objective (costs one extra forward operator per step) and
+ * the relative change; entries of steps not taken (early stop) are left as
+ * they were.  Tolerances are evaluated on the device: the call never
+ * synchronises.  CG scalars (alpha, beta, residual norms) are reduced in FP64.
+ */
+MRI_API int mri_admm_reconstruct(mri_plan *plan, const mri_c64 *kspace, const mri_c64 *coil_maps,
+                                 const mri_admm_params *params, mri_c64 *image_out,
+                                 double *objective_hist, double *alpha_hist, mri_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Diagnostics (not in the paper): kernel accounting used by benchmarks.
+ * ------------------------------------------------------------------------- */
+
+/* Enable (1) or disable (0) CUDA-event timing of the two product kernels of
+ * this plan (forward Eq. 1 and adjoint): every launch is bracketed by events
+ * on the launching stream. */
+MRI_API int mri_plan_set_timing(mri_plan *plan, int enable);
+
+/* Total milliseconds and launch counts of the timed forward and adjoint
+ * product kernels since the last read (nullable outputs); waits for the
+ * recorded events and then forgets them. */
+MRI_API int mri_plan_read_timing(mri_plan *plan, double *fwd_ms, long long *fwd_launches, double *adj_ms,
+                                 long long *adj_launches);
+
+/* Number of kernels this plan has enqueued since creation. */
+MRI_API long long mri_plan_launch_count(const mri_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRIRECON_H */

@@ -58,6 +58,7 @@ def _load():
         D = ctypes.c_double
         lib.orc_forward.argtypes = [I, I, I, I, P, P, P, P]
         lib.orc_adjoint.argtypes = [I, I, I, I, P, P, P, P]
+        lib.orc_adjoint_at.argtypes = [I, I, I, I, P, P, P, I, P, P]
         lib.orc_tv_forward.argtypes = [I, I, P, P]
         lib.orc_tv_adjoint.argtypes = [I, I, P, P]
         lib.orc_shrink.argtypes = [I, D, P, P]
@@ -113,6 +114,20 @@ def adjoint(traj, kspace, maps):
     nk = traj.shape[0]
     out = np.empty((nx, ny), np.complex128)
     lib.orc_adjoint(nx, ny, nk, nc, _p(traj), _p(kspace), _p(maps), _p(out))
+    return out
+
+
+def adjoint_at(traj, kspace, maps, pixels):
+    """The adjoint of Eq. 1 at the flat pixel indices ``pixels`` (``i*ny + j``) only."""
+    lib = _load()
+    traj = _c(traj, np.float64)
+    kspace = _c(kspace)
+    maps = _c(maps)
+    pix = np.ascontiguousarray(pixels, dtype=np.int32)
+    nc, nx, ny = maps.shape
+    out = np.empty(pix.size, np.complex128)
+    lib.orc_adjoint_at(nx, ny, traj.shape[0], nc, _p(traj), _p(kspace), _p(maps), int(pix.size), _p(pix),
+                       _p(out))
     return out
 
 

@@ -130,6 +130,34 @@ void orc_adjoint(int nx, int ny, int nk, int nc, const double *traj,
     }
 }
 
+/* The adjoint of Eq. 1 evaluated only at the npick pixels listed in pix
+ * (flat indices i*ny + j); out[q] receives the value at pix[q].  Same sum as
+ * orc_adjoint, for spot checks of large problems. */
+void orc_adjoint_at(int nx, int ny, int nk, int nc, const double *traj, const double *kspace,
+                    const double *maps, int npick, const int *pix, double *out) {
+    const cpx *d = (const cpx *)kspace;
+    const cpx *s = (const cpx *)maps;
+    cpx *x = (cpx *)out;
+    const int npix = nx * ny;
+#pragma omp parallel
+    {
+        cpx *acc = (cpx *)malloc(sizeof(cpx) * (size_t)nc);
+#pragma omp for schedule(static)
+        for (int q = 0; q < npick; ++q) {
+            const int n = pix[q], i = n / ny, j = n % ny;
+            for (int c = 0; c < nc; ++c) { acc[c].re = 0.0; acc[c].im = 0.0; }
+            for (int kk = 0; kk < nk; ++kk) {
+                cpx e = cconj(phasor_fwd(traj[2 * kk] * coord(i, nx) + traj[2 * kk + 1] * coord(j, ny)));
+                for (int c = 0; c < nc; ++c) acc[c] = cadd(acc[c], cmul(d[(size_t)c * nk + kk], e));
+            }
+            cpx o = {0.0, 0.0};
+            for (int c = 0; c < nc; ++c) o = cadd(o, cmul(cconj(s[(size_t)c * npix + n]), acc[c]));
+            x[q] = o;
+        }
+        free(acc);
+    }
+}
+
 /* Theta: first-order forward differences along each axis (conv1d with kernel
  * [-1, 1], zero padding past the last pixel).  g is [2][nx][ny]. */
 void orc_tv_forward(int nx, int ny, const double *image, double *grad) {

@@ -1,0 +1,260 @@
+"""Python binding of libmrirecon (GB300 / sm_103a MRI reconstruction).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libmrirecon.so``.  PyTorch supplies device memory and the current
+stream.  The functions mirror the C entry points of ``include/mrirecon.h``:
+
+* :class:`Plan`            -- ``mri_plan_create`` / ``mri_plan_set_trajectory`` /
+  ``mri_plan_destroy`` (DFT factor generation, Alg. 1)
+* :func:`nudft_forward`    -- Eq. 1-2
+* :func:`nudft_adjoint`    -- adjoint of Eq. 1 with coil combination
+* :func:`normal_op`        -- Eq. 11
+* :func:`tv_forward`, :func:`tv_adjoint` -- the finite-difference transform Theta
+* :func:`soft_threshold`   -- Eq. 9
+* :func:`admm_reconstruct` -- Alg. 4
+
+Tensors are CUDA, contiguous, complex64 (images ``[nx, ny]``, coil maps
+``[nc, nx, ny]``, k-space ``[nc, nk]``) or float32 (trajectory ``[nk, 2]``).
+If the shared library is missing the import fails loudly: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libmrirecon.so")
+
+MRI_OK = 0
+MRI_ERR_INVALID = -1
+MRI_ERR_NOMEM = -2
+MRI_ERR_CUDA = -3
+MRI_ERR_TIMEOUT = -4
+MRI_ERR_UNSUPPORTED = -5
+
+MRI_FP32 = 0
+MRI_BF16X3 = 2
+PRECISIONS = {"fp32": MRI_FP32, "bf16x3": MRI_BF16X3}
+
+
+class MriError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mrirecon error {code}: {msg}")
+        self.code = code
+
+
+class AdmmParams(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_float), ("beta", ctypes.c_float), ("admm_iters", ctypes.c_int),
+                ("cg_iters", ctypes.c_int), ("rtol", ctypes.c_double), ("atol", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load ``libmrirecon.so``; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libmrirecon.so not built ({path}); run paper_2006_14080_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I, F, D, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_double, ctypes.c_size_t
+    sigs = {
+        "mri_last_error": ([], ctypes.c_char_p),
+        "mri_version": ([], I),
+        "mri_plan_create": ([ctypes.POINTER(P), I, I, I, I, P, I, P], I),
+        "mri_plan_set_trajectory": ([P, P, P], I),
+        "mri_plan_destroy": ([P], I),
+        "mri_plan_sync_status": ([P, P], I),
+        "mri_plan_device_bytes": ([P], Z),
+        "mri_nudft_forward": ([P, P, P, P, P], I),
+        "mri_nudft_adjoint": ([P, P, P, P, P], I),
+        "mri_normal_op": ([P, P, P, F, P, P], I),
+        "mri_tv_forward": ([I, I, P, P, P], I),
+        "mri_tv_adjoint": ([I, I, P, P, P], I),
+        "mri_soft_threshold": ([I, F, P, P, P], I),
+        "mri_admm_reconstruct": ([P, P, P, ctypes.POINTER(AdmmParams), P, P, P, P], I),
+        "mri_plan_set_timing": ([P, I], I),
+        "mri_plan_read_timing": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
+                                  ctypes.POINTER(ctypes.c_longlong)], I),
+        "mri_plan_launch_count": ([P], ctypes.c_longlong),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != MRI_OK:
+        raise MriError(rc, load().mri_last_error().decode())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t: torch.Tensor, dtype, shape, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Plan:
+    """DFT factors for one trajectory plus all workspace (``mri_plan``)."""
+
+    def __init__(self, nx: int, ny: int, nc: int, traj: torch.Tensor, precision: str = "bf16x3", stream=None):
+        lib = load()
+        nk = int(traj.shape[0])
+        _need(traj, torch.float32, (nk, 2), "traj")
+        self.nx, self.ny, self.nc, self.nk = int(nx), int(ny), int(nc), nk
+        self.precision = precision
+        h = ctypes.c_void_p()
+        _check(lib.mri_plan_create(ctypes.byref(h), self.nx, self.ny, nk, self.nc, _ptr(traj),
+                                   PRECISIONS[precision], _stream(stream)))
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("plan is closed")
+        return self._h
+
+    def set_trajectory(self, traj: torch.Tensor, stream=None):
+        _need(traj, torch.float32, (self.nk, 2), "traj")
+        _check(load().mri_plan_set_trajectory(self.handle, _ptr(traj), _stream(stream)))
+
+    def sync_status(self, stream=None):
+        _check(load().mri_plan_sync_status(self.handle, _stream(stream)))
+
+    def device_bytes(self) -> int:
+        return int(load().mri_plan_device_bytes(self.handle))
+
+    def set_timing(self, enable: bool = True):
+        _check(load().mri_plan_set_timing(self.handle, int(bool(enable))))
+
+    def read_timing(self):
+        """``{"fwd_ms", "fwd_launches", "adj_ms", "adj_launches"}`` since the last read."""
+        fm, am = ctypes.c_double(), ctypes.c_double()
+        fn, an = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(load().mri_plan_read_timing(self.handle, ctypes.byref(fm), ctypes.byref(fn), ctypes.byref(am),
+                                           ctypes.byref(an)))
+        return {"fwd_ms": fm.value, "fwd_launches": fn.value, "adj_ms": am.value, "adj_launches": an.value}
+
+    def launch_count(self) -> int:
+        return int(load().mri_plan_launch_count(self.handle))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().mri_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def nudft_forward(plan: Plan, image, coil_maps, out=None, stream=None):
+    _need(image, torch.complex64, (plan.nx, plan.ny), "image")
+    _need(coil_maps, torch.complex64, (plan.nc, plan.nx, plan.ny), "coil_maps")
+    if out is None:
+        out = torch.empty((plan.nc, plan.nk), dtype=torch.complex64, device=image.device)
+    _need(out, torch.complex64, (plan.nc, plan.nk), "kspace")
+    _check(load().mri_nudft_forward(plan.handle, _ptr(image), _ptr(coil_maps), _ptr(out), _stream(stream)))
+    return out
+
+
+def nudft_adjoint(plan: Plan, kspace, coil_maps, out=None, stream=None):
+    _need(kspace, torch.complex64, (plan.nc, plan.nk), "kspace")
+    _need(coil_maps, torch.complex64, (plan.nc, plan.nx, plan.ny), "coil_maps")
+    if out is None:
+        out = torch.empty((plan.nx, plan.ny), dtype=torch.complex64, device=kspace.device)
+    _need(out, torch.complex64, (plan.nx, plan.ny), "image")
+    _check(load().mri_nudft_adjoint(plan.handle, _ptr(kspace), _ptr(coil_maps), _ptr(out), _stream(stream)))
+    return out
+
+
+def normal_op(plan: Plan, image, coil_maps, beta: float = 0.0, out=None, stream=None):
+    _need(image, torch.complex64, (plan.nx, plan.ny), "image")
+    _need(coil_maps, torch.complex64, (plan.nc, plan.nx, plan.ny), "coil_maps")
+    if out is None:
+        out = torch.empty_like(image)
+    _need(out, torch.complex64, (plan.nx, plan.ny), "out")
+    _check(load().mri_normal_op(plan.handle, _ptr(image), _ptr(coil_maps), float(beta), _ptr(out),
+                                _stream(stream)))
+    return out
+
+
+def tv_forward(image, out=None, stream=None):
+    nx, ny = image.shape
+    _need(image, torch.complex64, (nx, ny), "image")
+    if out is None:
+        out = torch.empty((2, nx, ny), dtype=torch.complex64, device=image.device)
+    _need(out, torch.complex64, (2, nx, ny), "grad")
+    _check(load().mri_tv_forward(nx, ny, _ptr(image), _ptr(out), _stream(stream)))
+    return out
+
+
+def tv_adjoint(grad, out=None, stream=None):
+    _, nx, ny = grad.shape
+    _need(grad, torch.complex64, (2, nx, ny), "grad")
+    if out is None:
+        out = torch.empty((nx, ny), dtype=torch.complex64, device=grad.device)
+    _need(out, torch.complex64, (nx, ny), "image")
+    _check(load().mri_tv_adjoint(nx, ny, _ptr(grad), _ptr(out), _stream(stream)))
+    return out
+
+
+def soft_threshold(x, t: float, out=None, stream=None):
+    _need(x, torch.complex64, tuple(x.shape), "x")
+    if out is None:
+        out = torch.empty_like(x)
+    _need(out, torch.complex64, tuple(x.shape), "out")
+    _check(load().mri_soft_threshold(x.numel(), float(t), _ptr(x), _ptr(out), _stream(stream)))
+    return out
+
+
+def admm_reconstruct(plan: Plan, kspace, coil_maps, lam: float, beta: float, admm_iters: int, cg_iters: int,
+                     rtol: float = 0.0, atol: float = 0.0, out=None, objective_hist=None, alpha_hist=None,
+                     stream=None):
+    """Alg. 4.  ``objective_hist`` / ``alpha_hist``: optional CUDA float64
+    tensors of ``admm_iters`` entries that receive the Eq. 3 objective and the
+    relative change after each outer step."""
+    _need(kspace, torch.complex64, (plan.nc, plan.nk), "kspace")
+    _need(coil_maps, torch.complex64, (plan.nc, plan.nx, plan.ny), "coil_maps")
+    if out is None:
+        out = torch.empty((plan.nx, plan.ny), dtype=torch.complex64, device=kspace.device)
+    _need(out, torch.complex64, (plan.nx, plan.ny), "image_out")
+    for h, name in ((objective_hist, "objective_hist"), (alpha_hist, "alpha_hist")):
+        if h is not None:
+            _need(h, torch.float64, (admm_iters,), name)
+    prm = AdmmParams(float(lam), float(beta), int(admm_iters), int(cg_iters), float(rtol), float(atol))
+    _check(load().mri_admm_reconstruct(plan.handle, _ptr(kspace), _ptr(coil_maps), ctypes.byref(prm), _ptr(out),
+                                       _ptr(objective_hist), _ptr(alpha_hist), _stream(stream)))
+    return out

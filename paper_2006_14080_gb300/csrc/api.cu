@@ -1,0 +1,430 @@
+// C-ABI entry points of libmrirecon: argument checks, plan and workspace
+// management, and the host-side sequencing of the reconstruction (Alg. 4 with
+// Alg. 2 inside), all enqueued on the caller's stream without synchronising.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace mri {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+
+int fail(int code, const std::string &msg) {
+    set_error(msg);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(MRI_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define MRI_CUDA_TRY(expr)                                  \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return cuda_fail(_e, #expr); \
+    } while (0)
+
+template <typename T>
+int dev_alloc(mri_plan *p, T **ptr, size_t count) {
+    if (count == 0) {
+        *ptr = nullptr;
+        return MRI_OK;
+    }
+    cudaError_t e = cudaMalloc((void **)ptr, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return fail(MRI_ERR_NOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+                                       " bytes failed: " + cudaGetErrorString(e));
+    }
+    p->bytes += count * sizeof(T);
+    return MRI_OK;
+}
+
+void free_plan(mri_plan *p) {
+    if (!p) return;
+    void *bufs[] = {p->ax,  p->ay,  p->axT,  p->ayT,   p->afwd_hi, p->afwd_lo, p->badj_hi, p->badj_lo,
+                    p->bfwd_hi, p->bfwd_lo, p->bsx, p->y, p->part, p->x, p->xprev, p->r,
+                    p->d,   p->ad,  p->b,    p->fhd,   p->mu,      p->eta,     p->partials, p->scal};
+    for (void *q : bufs)
+        if (q) cudaFree(q);
+    for (cudaEvent_t e : p->ev_free) cudaEventDestroy(e);
+    for (auto *list : {&p->ev_fwd, &p->ev_adj})
+        for (auto &pr : *list) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+    delete p;
+}
+
+// Number of k-space splits of the adjoint product: enough independent work
+// units to fill the GPU a few times, chosen from the problem's own shape and
+// the SM count only (so a reconstruction is computed identically alone or
+// alongside others).
+int choose_ksplit_fp32(const mri_plan *p, int *samples_per_split) {
+    const int tiles = ceil_div(p->nx, 64) * ceil_div(p->ny, 64) * p->nc;
+    const int target = 2 * p->num_sms;
+    int split = std::max(1, std::min(ceil_div(target, tiles), ceil_div(p->nk, 256)));
+    split = std::min(split, 64);
+    int per = round_up(ceil_div(p->nk, split), 16);
+    split = ceil_div(p->nk, per);
+    *samples_per_split = per;
+    return split;
+}
+
+bool finite(float v) { return isfinite(v) != 0; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// operator sequences shared by the entry points
+// ---------------------------------------------------------------------------
+// Take a pair of timing events from the plan's pool (creating them as needed).
+static bool timing_arm(mri_plan *p) {
+    if (!p->timing) return false;
+    cudaEvent_t ev[2];
+    for (int q = 0; q < 2; ++q) {
+        if (!p->ev_free.empty()) {
+            ev[q] = p->ev_free.back();
+            p->ev_free.pop_back();
+        } else if (cudaEventCreate(&ev[q]) != cudaSuccess) {
+            cudaGetLastError();
+            if (q == 1) p->ev_free.push_back(ev[0]);
+            return false;
+        }
+    }
+    p->t_ev0 = ev[0];
+    p->t_ev1 = ev[1];
+    return true;
+}
+
+static void timing_disarm(mri_plan *p, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &list) {
+    list.emplace_back(p->t_ev0, p->t_ev1);
+    p->t_ev0 = p->t_ev1 = nullptr;
+}
+
+static cudaError_t op_forward(mri_plan *p, const float2 *image, const float2 *maps, float2 *out, int skip,
+                              cudaStream_t s) {
+    const bool timed = timing_arm(p);
+    cudaError_t e = p->precision == MRI_BF16X3 ? launch_fwd_tc(p, image, maps, out, skip, s)
+                                               : launch_fwd_fp32(p, image, maps, out, skip, s);
+    if (timed) timing_disarm(p, p->ev_fwd);
+    return e;
+}
+
+static cudaError_t op_adjoint_partials(mri_plan *p, const float2 *kspace, int skip, cudaStream_t s) {
+    const bool timed = timing_arm(p);
+    cudaError_t e = p->precision == MRI_BF16X3 ? launch_adj_tc(p, kspace, skip, s) : launch_adj_fp32(p, kspace, skip, s);
+    if (timed) timing_disarm(p, p->ev_adj);
+    return e;
+}
+
+// out = F^H F src (+ half_beta Theta^H Theta src) (+ CG dot)
+static cudaError_t op_normal(mri_plan *p, const float2 *src, const float2 *maps, float2 *out, float half_beta,
+                             bool cg_dot, int skip, cudaStream_t s) {
+    cudaError_t e = op_forward(p, src, maps, p->y, skip, s);
+    if (e != cudaSuccess) return e;
+    e = op_adjoint_partials(p, p->y, skip, s);
+    if (e != cudaSuccess) return e;
+    ReduceEpilogue ep;
+    ep.tv_src = half_beta != 0.f ? src : nullptr;
+    ep.half_beta = half_beta;
+    ep.dot_src = cg_dot ? src : nullptr;
+    ep.skip = skip;
+    p->launches += 1;
+    return launch_adj_reduce(p, maps, out, ep, s);
+}
+
+}  // namespace mri
+
+using namespace mri;
+
+extern "C" {
+
+MRI_API const char *mri_last_error(void) { return g_last_error.c_str(); }
+
+MRI_API int mri_version(void) { return 100; }
+
+MRI_API int mri_plan_create(mri_plan **out, int nx, int ny, int nk, int nc, const float *traj, int precision,
+                            mri_stream_t stream) {
+    if (!out) return fail(MRI_ERR_INVALID, "plan output pointer is null");
+    *out = nullptr;
+    if (nx <= 0 || ny <= 0 || nk <= 0 || nc <= 0) return fail(MRI_ERR_INVALID, "dimensions must be positive");
+    if ((long long)nx * ny > (1LL << 26) || nk > (1 << 28) || nc > 4096)
+        return fail(MRI_ERR_INVALID, "dimensions too large");
+    if (!traj) return fail(MRI_ERR_INVALID, "trajectory pointer is null");
+    if (precision != MRI_FP32 && precision != MRI_BF16X3) return fail(MRI_ERR_INVALID, "unknown precision");
+    cudaStream_t s = (cudaStream_t)stream;
+
+    mri_plan *p = new mri_plan();
+    p->nx = nx;
+    p->ny = ny;
+    p->nk = nk;
+    p->nc = nc;
+    p->precision = precision;
+    {
+        cudaError_t e0 = cudaGetDevice(&p->device);
+        if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+        if (e0 != cudaSuccess) {
+            delete p;
+            return cuda_fail(e0, "device query");
+        }
+    }
+    p->nx_pad = round_up(nx, 64);
+    p->ny_pad = round_up(ny, 16);
+    p->kx = round_up(2 * nx, 64);
+    p->kk = round_up(2 * nk, 64);
+
+    int rc = MRI_OK;
+    const size_t npix = (size_t)nx * ny;
+    if (precision == MRI_BF16X3) {
+        std::string why;
+        if (!tc_supported(p, &why)) {
+            delete p;
+            return fail(MRI_ERR_UNSUPPORTED, "BF16x3 tensor-core path: " + why);
+        }
+        rc = tc_plan_tiling(p);
+        if (rc != MRI_OK) {
+            delete p;
+            return fail(rc, "BF16x3 tensor-core path: shared-memory plan does not fit");
+        }
+        if (rc == MRI_OK) rc = dev_alloc(p, &p->axT, (size_t)nx * nk);
+        if (rc == MRI_OK) rc = dev_alloc(p, &p->ayT, (size_t)ny * nk);
+        if (rc == MRI_OK) rc = dev_alloc(p, &p->afwd_hi, (size_t)2 * nk * p->kx);
+        if (rc == MRI_OK) rc = dev_alloc(p, &p->afwd_lo, (size_t)2 * nk * p->kx);
+        if (rc == MRI_OK) rc = dev_alloc(p, &p->badj_hi, (size_t)p->ny_pad * p->kk);
+        if (rc == MRI_OK) rc = dev_alloc(p, &p->badj_lo, (size_t)p->ny_pad * p->kk);
+        if (rc == MRI_OK) rc = dev_alloc(p, &p->bfwd_hi, (size_t)nc * p->ny_pad * p->kx);
+        if (rc == MRI_OK) rc = dev_alloc(p, &p->bfwd_lo, (size_t)nc * p->ny_pad * p->kx);
+    } else {
+        int per = 0;
+        p->ksplit = choose_ksplit_fp32(p, &per);
+        p->ksplit_blocks = per;
+        if (rc == MRI_OK) rc = dev_alloc(p, &p->ax, (size_t)nk * nx);
+        if (rc == MRI_OK) rc = dev_alloc(p, &p->ay, (size_t)nk * ny);
+        if (rc == MRI_OK) rc = dev_alloc(p, &p->bsx, (size_t)nc * npix);
+    }
+    if (rc == MRI_OK) rc = dev_alloc(p, &p->y, (size_t)nc * nk);
+    if (rc == MRI_OK) rc = dev_alloc(p, &p->part, (size_t)p->ksplit * nc * ny * p->nx_pad);
+    float2 **img_bufs[] = {&p->x, &p->xprev, &p->r, &p->d, &p->ad, &p->b, &p->fhd};
+    for (float2 **q : img_bufs)
+        if (rc == MRI_OK) rc = dev_alloc(p, q, npix);
+    if (rc == MRI_OK) rc = dev_alloc(p, &p->mu, 2 * npix);
+    if (rc == MRI_OK) rc = dev_alloc(p, &p->eta, 2 * npix);
+    // one slot pair per block of the largest reducing grid (element-wise
+    // kernels use at most 1024 blocks, the adjoint reduction one per 32x32 tile)
+    p->partials_cap = 2 * std::max(1024, ceil_div(nx, 32) * ceil_div(ny, 32));
+    if (rc == MRI_OK) rc = dev_alloc(p, &p->partials, (size_t)p->partials_cap);
+    if (rc == MRI_OK) rc = dev_alloc(p, &p->scal, 1);
+    if (rc != MRI_OK) {
+        free_plan(p);
+        return rc;
+    }
+    // zero padding of the tensor-core operands must stay zero
+    cudaError_t e = cudaSuccess;
+    if (precision == MRI_BF16X3) {
+        __nv_bfloat16 *zb[] = {p->afwd_hi, p->afwd_lo, p->badj_hi, p->badj_lo, p->bfwd_hi, p->bfwd_lo};
+        size_t zn[] = {(size_t)2 * nk * p->kx, (size_t)2 * nk * p->kx, (size_t)p->ny_pad * p->kk,
+                       (size_t)p->ny_pad * p->kk, (size_t)nc * p->ny_pad * p->kx, (size_t)nc * p->ny_pad * p->kx};
+        for (int q = 0; q < 6 && e == cudaSuccess; ++q) e = cudaMemsetAsync(zb[q], 0, zn[q] * 2, s);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->part, 0, (size_t)p->ksplit * nc * ny * p->nx_pad * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->scal, 0, sizeof(DevScalars), s);
+    if (e == cudaSuccess && precision == MRI_BF16X3) {
+        rc = tc_make_tensor_maps(p);
+        if (rc != MRI_OK) {
+            free_plan(p);
+            return rc;
+        }
+    }
+    if (e == cudaSuccess) e = launch_factors(p, traj, s);
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "plan initialisation");
+    }
+    *out = p;
+    return MRI_OK;
+}
+
+MRI_API int mri_plan_set_trajectory(mri_plan *p, const float *traj, mri_stream_t stream) {
+    if (!p || !traj) return fail(MRI_ERR_INVALID, "null plan or trajectory");
+    cudaError_t e = launch_factors(p, traj, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "factor generation");
+    p->launches += 2;
+    return MRI_OK;
+}
+
+MRI_API int mri_plan_destroy(mri_plan *p) {
+    if (!p) return MRI_OK;
+    cudaDeviceSynchronize();
+    free_plan(p);
+    return MRI_OK;
+}
+
+MRI_API int mri_plan_sync_status(mri_plan *p, mri_stream_t stream) {
+    if (!p) return fail(MRI_ERR_INVALID, "null plan");
+    MRI_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    int status = 0;
+    MRI_CUDA_TRY(cudaMemcpy(&status, &p->scal->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status != kStatusOk) {
+        int zero = 0;
+        MRI_CUDA_TRY(cudaMemcpy(&p->scal->status, &zero, sizeof(int), cudaMemcpyHostToDevice));
+        return fail(MRI_ERR_TIMEOUT, "a bounded device-side wait gave up (status " + std::to_string(status) + ")");
+    }
+    return MRI_OK;
+}
+
+MRI_API size_t mri_plan_device_bytes(const mri_plan *p) { return p ? p->bytes : 0; }
+
+MRI_API int mri_nudft_forward(mri_plan *p, const mri_c64 *image, const mri_c64 *maps, mri_c64 *kspace,
+                              mri_stream_t stream) {
+    if (!p || !image || !maps || !kspace) return fail(MRI_ERR_INVALID, "null argument");
+    cudaError_t e = op_forward(p, (const float2 *)image, (const float2 *)maps, (float2 *)kspace, kSkipNever,
+                               (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "forward operator");
+    return MRI_OK;
+}
+
+MRI_API int mri_nudft_adjoint(mri_plan *p, const mri_c64 *kspace, const mri_c64 *maps, mri_c64 *image,
+                              mri_stream_t stream) {
+    if (!p || !image || !maps || !kspace) return fail(MRI_ERR_INVALID, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = op_adjoint_partials(p, (const float2 *)kspace, kSkipNever, s);
+    if (e == cudaSuccess) e = launch_adj_reduce(p, (const float2 *)maps, (float2 *)image, ReduceEpilogue(), s);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint operator");
+    return MRI_OK;
+}
+
+MRI_API int mri_normal_op(mri_plan *p, const mri_c64 *image, const mri_c64 *maps, float beta, mri_c64 *out,
+                          mri_stream_t stream) {
+    if (!p || !image || !maps || !out) return fail(MRI_ERR_INVALID, "null argument");
+    if (!finite(beta) || beta < 0.f) return fail(MRI_ERR_INVALID, "beta must be finite and >= 0");
+    if ((const void *)image == (const void *)out) return fail(MRI_ERR_INVALID, "image and out must differ");
+    cudaError_t e = op_normal(p, (const float2 *)image, (const float2 *)maps, (float2 *)out, 0.5f * beta, false,
+                              kSkipNever, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "normal operator");
+    return MRI_OK;
+}
+
+MRI_API int mri_tv_forward(int nx, int ny, const mri_c64 *image, mri_c64 *grad, mri_stream_t stream) {
+    if (nx <= 0 || ny <= 0 || !image || !grad) return fail(MRI_ERR_INVALID, "bad argument");
+    cudaError_t e = launch_tv_forward(nx, ny, (const float2 *)image, (float2 *)grad, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tv_forward");
+    return MRI_OK;
+}
+
+MRI_API int mri_tv_adjoint(int nx, int ny, const mri_c64 *grad, mri_c64 *image, mri_stream_t stream) {
+    if (nx <= 0 || ny <= 0 || !image || !grad) return fail(MRI_ERR_INVALID, "bad argument");
+    cudaError_t e = launch_tv_adjoint(nx, ny, (const float2 *)grad, (float2 *)image, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tv_adjoint");
+    return MRI_OK;
+}
+
+MRI_API int mri_soft_threshold(int n, float t, const mri_c64 *in, mri_c64 *out, mri_stream_t stream) {
+    if (n < 0 || !in || !out || !finite(t) || t < 0.f) return fail(MRI_ERR_INVALID, "bad argument");
+    if (n == 0) return MRI_OK;
+    cudaError_t e = launch_shrink(n, t, (const float2 *)in, (float2 *)out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "soft_threshold");
+    return MRI_OK;
+}
+
+MRI_API int mri_admm_reconstruct(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in,
+                                 const mri_admm_params *prm, mri_c64 *image_out, double *objective_hist,
+                                 double *alpha_hist, mri_stream_t stream) {
+    if (!p || !kspace_in || !maps_in || !prm || !image_out) return fail(MRI_ERR_INVALID, "null argument");
+    if (!finite(prm->lambda) || prm->lambda < 0.f) return fail(MRI_ERR_INVALID, "lambda must be finite and >= 0");
+    if (!finite(prm->beta) || !(prm->beta > 0.f)) return fail(MRI_ERR_INVALID, "beta must be finite and > 0");
+    if (prm->admm_iters < 0 || prm->cg_iters < 0) return fail(MRI_ERR_INVALID, "iteration counts must be >= 0");
+    if (!isfinite(prm->rtol) || prm->rtol < 0 || !isfinite(prm->atol) || prm->atol < 0)
+        return fail(MRI_ERR_INVALID, "tolerances must be finite and >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const float2 *kspace = (const float2 *)kspace_in;
+    const float2 *maps = (const float2 *)maps_in;
+    const size_t npix = (size_t)p->nx * p->ny;
+    const float half_beta = 0.5f * prm->beta;
+    const float thresh = prm->lambda / prm->beta;
+
+#define STEP(expr)                                                  \
+    do {                                                            \
+        cudaError_t _e = (expr);                                    \
+        if (_e != cudaSuccess) return cuda_fail(_e, "admm: " #expr); \
+    } while (0)
+#define KERNEL(expr)      \
+    do {                  \
+        STEP(expr);       \
+        p->launches += 1; \
+    } while (0)
+
+    KERNEL(launch_admm_reset(p, prm->atol, prm->rtol, s));
+    STEP(cudaMemsetAsync(p->x, 0, npix * sizeof(float2), s));
+    STEP(cudaMemsetAsync(p->eta, 0, 2 * npix * sizeof(float2), s));
+    // F^H d, once per reconstruction (Section IV-C: the right-hand side stays
+    // fixed through the CG iterations)
+    STEP(op_adjoint_partials(p, kspace, kSkipNever, s));
+    KERNEL(launch_adj_reduce(p, maps, p->fhd, ReduceEpilogue(), s));
+    for (int m = 0; m < prm->admm_iters; ++m) {
+        KERNEL(launch_admm_mu(p, thresh, s));        // Eq. 8
+        KERNEL(launch_admm_rhs(p, half_beta, s));    // Eq. 12
+        STEP(op_normal(p, p->x, maps, p->ad, half_beta, false, kSkipAdmm, s));  // A x0
+        KERNEL(launch_cg_init(p, s));
+        for (int it = 0; it < prm->cg_iters; ++it) {
+            if (it > 0) KERNEL(launch_cg_direction(p, s));
+            STEP(op_normal(p, p->d, maps, p->ad, half_beta, true, kSkipCg, s));  // A d, alpha
+            KERNEL(launch_cg_update(p, s));
+        }
+        KERNEL(launch_admm_dual(p, alpha_hist, m, s));  // Eq. 8 (dual), Alg. 4 relative change
+        if (objective_hist) {
+            STEP(op_forward(p, p->x, maps, p->y, kSkipStep, s));
+            KERNEL(launch_objective(p, kspace, prm->lambda, objective_hist, m, s));
+        }
+    }
+    STEP(cudaMemcpyAsync(image_out, p->x, npix * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+#undef KERNEL
+#undef STEP
+    return MRI_OK;
+}
+
+MRI_API int mri_plan_set_timing(mri_plan *p, int enable) {
+    if (!p) return fail(MRI_ERR_INVALID, "null plan");
+    p->timing = enable != 0;
+    return MRI_OK;
+}
+
+MRI_API int mri_plan_read_timing(mri_plan *p, double *fwd_ms, long long *fwd_launches, double *adj_ms,
+                                 long long *adj_launches) {
+    if (!p) return fail(MRI_ERR_INVALID, "null plan");
+    double sums[2] = {0.0, 0.0};
+    long long counts[2] = {0, 0};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *lists[2] = {&p->ev_fwd, &p->ev_adj};
+    for (int q = 0; q < 2; ++q) {
+        for (auto &pr : *lists[q]) {
+            float ms = 0.f;
+            cudaError_t e = cudaEventSynchronize(pr.second);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+            if (e != cudaSuccess) return cuda_fail(e, "read_timing");
+            sums[q] += ms;
+            counts[q] += 1;
+            p->ev_free.push_back(pr.first);
+            p->ev_free.push_back(pr.second);
+        }
+        lists[q]->clear();
+    }
+    if (fwd_ms) *fwd_ms = sums[0];
+    if (fwd_launches) *fwd_launches = counts[0];
+    if (adj_ms) *adj_ms = sums[1];
+    if (adj_launches) *adj_launches = counts[1];
+    return MRI_OK;
+}
+
+MRI_API long long mri_plan_launch_count(const mri_plan *p) { return p ? p->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Generation of the separable DFT factors (Alg. 1, per axis):
+//   A_x[k][i] = exp(-i 2 pi kx_k x_i),  A_y[k][j] = exp(-i 2 pi ky_k y_j),
+// x_i = i - nx/2, y_j = j - ny/2.  The phase kx_k * x_i is formed in FP64
+// (exact: a 24-bit mantissa times a small integer) and reduced to [-1/2, 1/2]
+// by subtracting the nearest integer, also exact; only then is it rounded to
+// FP32 for sincospif.  Besides the FP32 factors, the kernel writes the
+// tensor-core operands: BF16 hi/lo splits of the real embedding of A_x
+// (forward product) and of conj(A_y) (adjoint product).
+#include "common.cuh"
+#include "internal.h"
+
+namespace mri {
+
+namespace {
+
+__device__ __forceinline__ float2 dft_phasor(float k, int idx, int n) {
+    const double t = (double)k * (double)(idx - n / 2);
+    const double f = t - rint(t);
+    float s, c;
+    sincospif(-2.0f * (float)f, &s, &c);
+    return make_float2(c, s);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// hi = bf16(v), lo = bf16(v - hi) for the two halves of a pair.
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t &hi, uint32_t &lo) {
+    __nv_bfloat16 ah = __float2bfloat16_rn(a), bh = __float2bfloat16_rn(b);
+    __nv_bfloat16 al = __float2bfloat16_rn(a - __bfloat162float(ah));
+    __nv_bfloat16 bl = __float2bfloat16_rn(b - __bfloat162float(bh));
+    hi = pack_bf16(ah, bh);
+    lo = pack_bf16(al, bl);
+}
+
+// One 32 (samples) x 32 (pixel index) tile of one axis.  block = (32, 8).
+// F [nk][n] and FT [n][nk] are the FP32 factor and its transpose (either may
+// be null).  emb_hi/lo (nullable) receive the forward-product embedding
+// rows 2k: (Re, -Im), 2k+1: (Im, Re) at columns 2*idx, leading dim ld_emb.
+// cemb_hi/lo (nullable) receive the adjoint-product embedding of conj(F):
+// row idx, columns 2k, 2k+1 = (Re, -Im), leading dim ld_cemb.
+__global__ void factor_tile_kernel(const float *__restrict__ traj, int axis, int n, int nk,
+                                   float2 *__restrict__ F, float2 *__restrict__ FT,
+                                   uint32_t *__restrict__ emb_hi, uint32_t *__restrict__ emb_lo, int ld_emb,
+                                   uint32_t *__restrict__ cemb_hi, uint32_t *__restrict__ cemb_lo,
+                                   int ld_cemb) {
+    __shared__ float2 tile[32][33];
+    const int k0 = blockIdx.x * 32, p0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    // pass 1: threads along the pixel index (coalesced rows of F and of the forward embedding)
+    for (int q = ty; q < 32; q += 8) {
+        const int k = k0 + q, idx = p0 + tx;
+        float2 v = make_float2(0.f, 0.f);
+        if (k < nk && idx < n) {
+            v = dft_phasor(traj[2 * k + axis], idx, n);
+            if (F) F[(size_t)k * n + idx] = v;
+            if (emb_hi) {
+                uint32_t h, l;
+                // row 2k: (Re, -Im)
+                split_pair(v.x, -v.y, h, l);
+                emb_hi[((size_t)(2 * k) * ld_emb) / 2 + idx] = h;
+                emb_lo[((size_t)(2 * k) * ld_emb) / 2 + idx] = l;
+                // row 2k+1: (Im, Re)
+                split_pair(v.y, v.x, h, l);
+                emb_hi[((size_t)(2 * k + 1) * ld_emb) / 2 + idx] = h;
+                emb_lo[((size_t)(2 * k + 1) * ld_emb) / 2 + idx] = l;
+            }
+        }
+        tile[q][tx] = v;
+    }
+    __syncthreads();
+    // pass 2: threads along the sample index (coalesced rows of FT and of the adjoint embedding)
+    for (int q = ty; q < 32; q += 8) {
+        const int idx = p0 + q, k = k0 + tx;
+        if (k < nk && idx < n) {
+            const float2 v = tile[tx][q];
+            if (FT) FT[(size_t)idx * nk + k] = v;
+            if (cemb_hi) {
+                uint32_t h, l;
+                // conj(F) = (Re, -Im) at columns 2k, 2k+1
+                split_pair(v.x, -v.y, h, l);
+                cemb_hi[((size_t)idx * ld_cemb) / 2 + k] = h;
+                cemb_lo[((size_t)idx * ld_cemb) / 2 + k] = l;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_factors(mri_plan *p, const float *traj, cudaStream_t s) {
+    dim3 block(32, 8);
+    {
+        dim3 grid(ceil_div(p->nk, 32), ceil_div(p->nx, 32));
+        factor_tile_kernel<<<grid, block, 0, s>>>(traj, 0, p->nx, p->nk, p->ax, p->axT,
+                                                  (uint32_t *)p->afwd_hi, (uint32_t *)p->afwd_lo, p->kx,
+                                                  nullptr, nullptr, 0);
+    }
+    {
+        dim3 grid(ceil_div(p->nk, 32), ceil_div(p->ny, 32));
+        factor_tile_kernel<<<grid, block, 0, s>>>(traj, 1, p->ny, p->nk, p->ay, p->ayT, nullptr, nullptr, 0,
+                                                  (uint32_t *)p->badj_hi, (uint32_t *)p->badj_lo, p->kk);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mri

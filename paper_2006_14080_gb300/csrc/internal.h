@@ -1,0 +1,155 @@
+// Internal declarations of the mrirecon library: the plan object and the
+// launchers each translation unit provides.  Not part of the public ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "mrirecon.h"
+
+namespace mri {
+
+// Scalars of the solver, resident on the device so that no step of the
+// reconstruction waits on the host.
+struct DevScalars {
+    double tau;         // ||r||^2 of the current CG iterate (Alg. 2)
+    double alpha;       // CG step length tau / Re<d, A d>
+    double beta_cg;     // CG direction coefficient tau' / tau
+    double admm_alpha;  // relative change ||x'-x||^2 / ||x'||^2 (Alg. 4)
+    double atol2;       // atol^2
+    double rtol2;       // rtol^2
+    int cg_done;        // CG has met its tolerance for the current x-update
+    int admm_done;      // ADMM has met its tolerance
+    int status;         // 0, or a device-side failure code (see kStatus*)
+    int step_active;    // the current ADMM step runs (ADMM had not stopped when it began)
+    unsigned counters[8];  // grid-reduction tickets, one per reduction site
+};
+
+enum : int { kStatusOk = 0, kStatusTimeout = 1 };
+enum SkipMode : int { kSkipNever = 0, kSkipAdmm = 1, kSkipCg = 2, kSkipStep = 3 };
+
+__device__ __forceinline__ bool should_skip(const DevScalars *s, int mode) {
+    if (mode == kSkipNever || s == nullptr) return false;
+    if (mode == kSkipStep) return !s->step_active;
+    if (s->admm_done) return true;
+    return mode == kSkipCg && s->cg_done;
+}
+
+enum Counter : int { kCntDot = 0, kCntTau = 1, kCntInit = 2, kCntDual = 3, kCntObj = 4 };
+
+// Tile constants of the tensor-core kernels.
+constexpr int kTcBlockM = 128;   // UMMA M (rows of the real-embedded operand)
+constexpr int kTcBlockK = 64;    // bf16 elements per 128-byte swizzled row
+
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace mri
+
+struct mri_plan {
+    int nx = 0, ny = 0, nk = 0, nc = 0, precision = 0;
+    int device = 0, num_sms = 0;
+
+    // FP32 factors (Alg. 1, separable): A_x[k][i], A_y[k][j]
+    float2 *ax = nullptr;   // [nk][nx]
+    float2 *ay = nullptr;   // [nk][ny]
+    // transposed FP32 factors used by the tensor-core path
+    float2 *axT = nullptr;  // [nx][nk]
+    float2 *ayT = nullptr;  // [ny][nk]
+
+    // BF16 hi/lo real-embedded operands (tensor-core path)
+    int kx = 0;       // round_up(2*nx, 64): K of the forward product
+    int kk = 0;       // round_up(2*nk, 64): K of the adjoint product
+    int ny_pad = 0;   // round_up(ny, 16): UMMA N granularity
+    int nx_pad = 0;   // round_up(nx, 64): image rows per adjoint M tile group
+    int fwd_coils_per_tile = 0, fwd_block_n = 0, fwd_n_tiles = 0, fwd_m_tiles = 0;
+    int adj_m_tiles = 0, adj_block_n = 0;
+    __nv_bfloat16 *afwd_hi = nullptr, *afwd_lo = nullptr;  // [2*nk][kx]
+    __nv_bfloat16 *badj_hi = nullptr, *badj_lo = nullptr;  // [ny_pad][kk]
+    __nv_bfloat16 *bfwd_hi = nullptr, *bfwd_lo = nullptr;  // [nc*ny_pad][kx]
+    CUtensorMap tm_afwd_hi, tm_afwd_lo, tm_bfwd_hi, tm_bfwd_lo, tm_badj_hi, tm_badj_lo;
+
+    // operator workspace
+    float2 *bsx = nullptr;    // [nc][nx][ny] S_c . x (FP32 path)
+    float2 *y = nullptr;      // [nc][nk]
+    float2 *part = nullptr;   // [ksplit][nc][ny][nx_pad] adjoint partial images
+    int ksplit = 1;           // k-space splits of the adjoint product
+    int ksplit_blocks = 0;    // K blocks per split (tensor path) or samples per split (FP32)
+
+    // solver state
+    float2 *x = nullptr, *xprev = nullptr, *r = nullptr, *d = nullptr, *ad = nullptr;
+    float2 *b = nullptr, *fhd = nullptr;                 // [nx][ny]
+    float2 *mu = nullptr, *eta = nullptr;                // [2][nx][ny]
+    double *partials = nullptr;                          // grid-reduction partials
+    int partials_cap = 0;                                // doubles
+    mri::DevScalars *scal = nullptr;
+
+    size_t bytes = 0;
+
+    // diagnostics: kernel launches issued on this plan, and optional CUDA-event
+    // timing of the two product kernels (see mri_plan_set_timing)
+    long long launches = 0;
+    bool timing = false;
+    cudaEvent_t t_ev0 = nullptr, t_ev1 = nullptr;  // set by the caller around one product launch
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_fwd, ev_adj;
+};
+
+// Record the timing events (when set) immediately around a product kernel.
+inline void timing_begin(mri_plan *p, cudaStream_t s) {
+    if (p->t_ev0) cudaEventRecord(p->t_ev0, s);
+}
+inline void timing_end(mri_plan *p, cudaStream_t s) {
+    if (p->t_ev1) cudaEventRecord(p->t_ev1, s);
+}
+
+namespace mri {
+
+void set_error(const std::string &msg);
+
+// factors.cu
+cudaError_t launch_factors(mri_plan *p, const float *traj, cudaStream_t s);
+
+// nudft_fp32.cu
+cudaError_t launch_fwd_fp32(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace,
+                            int skip, cudaStream_t s);
+cudaError_t launch_adj_fp32(mri_plan *p, const float2 *kspace, int skip, cudaStream_t s);
+
+// nudft_tc.cu
+bool tc_supported(const mri_plan *p, std::string *why);
+int tc_plan_tiling(mri_plan *p);       // tile shapes and k-space splits; MRI_* status
+int tc_make_tensor_maps(mri_plan *p);  // TMA descriptors of the allocated operands; MRI_* status
+cudaError_t launch_fwd_tc(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace,
+                          int skip, cudaStream_t s);
+cudaError_t launch_adj_tc(mri_plan *p, const float2 *kspace, int skip, cudaStream_t s);
+
+// solver.cu
+struct ReduceEpilogue {
+    const float2 *tv_src = nullptr;  // add half_beta * Theta^H Theta tv_src when non-null
+    float half_beta = 0.f;
+    const float2 *dot_src = nullptr; // when non-null: Re<dot_src, out> -> scal->alpha = tau / dot
+    int skip = kSkipNever;
+};
+cudaError_t launch_adj_reduce(mri_plan *p, const float2 *maps, float2 *out, const ReduceEpilogue &e,
+                              cudaStream_t s);
+cudaError_t launch_tv_forward(int nx, int ny, const float2 *x, float2 *g, cudaStream_t s);
+cudaError_t launch_tv_adjoint(int nx, int ny, const float2 *g, float2 *x, cudaStream_t s);
+cudaError_t launch_shrink(int n, float t, const float2 *in, float2 *out, cudaStream_t s);
+cudaError_t launch_admm_mu(mri_plan *p, float thresh, cudaStream_t s);
+cudaError_t launch_admm_rhs(mri_plan *p, float half_beta, cudaStream_t s);
+cudaError_t launch_cg_init(mri_plan *p, cudaStream_t s);
+cudaError_t launch_cg_update(mri_plan *p, cudaStream_t s);
+cudaError_t launch_cg_direction(mri_plan *p, cudaStream_t s);
+cudaError_t launch_admm_dual(mri_plan *p, double *alpha_hist, int m, cudaStream_t s);
+cudaError_t launch_objective(mri_plan *p, const float2 *kspace, float lambda, double *obj_hist, int m,
+                             cudaStream_t s);
+cudaError_t launch_admm_reset(mri_plan *p, double atol, double rtol, cudaStream_t s);
+
+}  // namespace mri

@@ -1,0 +1,109 @@
+"""End-to-end ADMM reconstructions on the GPU against the FP64 oracle.
+
+The oracle's reconstructions of the seeded workloads are stored under
+tests/golden/ by make_golden.py (which calls only the oracle).  The GPU runs
+the same fixed iteration counts from the same inputs; the bar is the target
+of the mixed-precision form: NRMSE <= 1e-3 of the final image against the
+FP64 image, for both the plain FP32 and the BF16x3 forms.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+NRMSE_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def mr():
+    import paper_2006_14080_gb300 as mr
+    mr.load()
+    return mr
+
+
+def _dev(a, dtype=torch.complex64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def _golden(problem):
+    path = os.path.join(GOLDEN, f"admm_{problem.name}.npz")
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not generated")
+    g = np.load(path)
+    d = oracle.measurements(problem)
+    # the regenerated measurement is the one the golden run used
+    assert abs(np.linalg.norm(d.astype(np.complex128)) - float(g["d_norm"])) <= 1e-9 * float(g["d_norm"])
+    assert np.array_equal(d.reshape(-1)[g["d_idx"]], g["d_samples"])
+    return g, d
+
+
+def _run(mr, p, d, precision, with_hist=True, rtol=0.0, atol=0.0, lam=None, beta=None, iters=None):
+    lam = p.lam if lam is None else lam
+    beta = p.beta if beta is None else beta
+    admm_iters, cg_iters = (p.admm_iters, p.cg_iters) if iters is None else iters
+    with mr.Plan(p.nx, p.ny, p.nc, _dev(p.traj, torch.float32), precision) as plan:
+        obj = torch.full((admm_iters,), -1.0, dtype=torch.float64, device="cuda") if with_hist else None
+        alp = torch.full((admm_iters,), -1.0, dtype=torch.float64, device="cuda") if with_hist else None
+        x = mr.admm_reconstruct(plan, _dev(d), _dev(p.maps), lam, beta, admm_iters, cg_iters,
+                                rtol=rtol, atol=atol, objective_hist=obj, alpha_hist=alp)
+        plan.sync_status()
+        return (x.cpu().numpy().astype(np.complex128),
+                None if obj is None else obj.cpu().numpy(), None if alp is None else alp.cpu().numpy())
+
+
+def _nrmse(x, ref):
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_admm_small_matches_oracle(mr, precision):
+    p = synth.config_small()
+    g, d = _golden(p)
+    x, obj, alp = _run(mr, p, d, precision)
+    assert _nrmse(x, g["x"]) <= NRMSE_TOL
+    # histories follow the oracle's
+    assert np.allclose(obj, g["objective"], rtol=1e-4)
+    assert np.all(np.diff(obj) <= 1e-6 * np.abs(obj[:-1]))
+    assert np.allclose(alp[1:], g["alpha"][1:], rtol=2e-2)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_admm_medium_matches_oracle(mr, precision):
+    p = synth.config_medium()
+    g, d = _golden(p)
+    x, _, _ = _run(mr, p, d, precision, with_hist=False)
+    err = _nrmse(x, g["x"])
+    print(f"medium workload {precision}: NRMSE vs FP64 oracle = {err:.3e}")
+    assert err <= NRMSE_TOL
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_admm_table1_tolerances_stop_like_oracle(mr, precision):
+    with open(os.path.join(GOLDEN, "table1_admm_params.json")) as fh:
+        t1 = json.load(fh)
+    p = synth.config_small()
+    d = oracle.measurements(p)
+    ref = oracle.admm(p.traj, p.maps, d, t1["lambda"], t1["beta"], t1["admm_max_iterations"],
+                      t1["cg_max_iterations"], rtol=t1["admm_rtol"], atol=t1["cg_atol"])
+    x, obj, alp = _run(mr, p, d, precision, lam=t1["lambda"], beta=t1["beta"],
+                       iters=(t1["admm_max_iterations"], t1["cg_max_iterations"]),
+                       rtol=t1["admm_rtol"], atol=t1["cg_atol"])
+    steps = int(np.sum(alp >= 0))
+    assert 1 <= steps <= t1["admm_max_iterations"]
+    assert steps == ref["steps"]
+    assert _nrmse(x, ref["x"]) <= 1e-2
+
+
+def test_admm_zero_iterations_returns_zero_image(mr):
+    p = synth.config_small()
+    d = oracle.measurements(p)
+    x, _, _ = _run(mr, p, d, "fp32", with_hist=False, iters=(0, 5))
+    assert np.all(x == 0)

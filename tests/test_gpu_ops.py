@@ -1,0 +1,159 @@
+"""GPU parity of every operator of the C-ABI against the FP64 oracle.
+
+Sizes span several tiles of both product kernels with ragged tails (image
+sides not multiples of 32/64, sample counts not multiples of 64).  Bars:
+relative L2 error of the DFT operators <= 2e-6 (FP32 FFMA path) and <= 1e-5
+(BF16x3 tensor path, the operator target); the image-space stencils are
+single FP32 roundings of exact differences, so they are held to 4 ulp of the
+field's maximum.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+OP_TOL = {"fp32": 2e-6, "bf16x3": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def mr():
+    import paper_2006_14080_gb300 as mr
+    mr.load()
+    return mr
+
+
+def _dev(a, dtype=torch.complex64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def _rel(a, b):
+    a = np.asarray(a, np.complex128)
+    b = np.asarray(b, np.complex128)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _case(nx, ny, nc, spokes, readout, seed):
+    rng = np.random.default_rng(seed)
+    maps = synth.coil_maps(rng, nx, ny, nc)
+    traj = synth.radial_trajectory(spokes, readout, golden=True)
+    x = synth.random_complex(rng, (nx, ny))
+    y = synth.random_complex(rng, (nc, traj.shape[0]))
+    return maps, traj, x, y
+
+
+SHAPES = [
+    # nx, ny, nc, spokes, readout
+    (40, 40, 3, 7, 100),      # ragged everywhere
+    (64, 48, 2, 16, 128),     # non-square, ny a multiple of 16 only
+    (100, 72, 5, 9, 61),      # odd sample count
+    (32, 32, 4, 16, 64),      # the small workload's shape
+]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_forward_adjoint_normal_match_oracle(mr, precision, shape):
+    nx, ny, nc, spokes, readout = shape
+    maps, traj, x, y = _case(nx, ny, nc, spokes, readout, seed=sum(shape))
+    tol = OP_TOL[precision]
+    with mr.Plan(nx, ny, nc, _dev(traj, torch.float32), precision) as plan:
+        dm, dx, dy = _dev(maps), _dev(x), _dev(y)
+        fwd = mr.nudft_forward(plan, dx, dm).cpu().numpy()
+        adj = mr.nudft_adjoint(plan, dy, dm).cpu().numpy()
+        nrm = mr.normal_op(plan, dx, dm, beta=0.8).cpu().numpy()
+        plan.sync_status()
+    assert _rel(fwd, oracle.forward(traj, x, maps)) <= tol
+    assert _rel(adj, oracle.adjoint(traj, y, maps)) <= tol
+    assert _rel(nrm, oracle.normal(traj, maps, 0.8, x)) <= 2 * tol
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_cartesian_grid_gives_centred_fft(mr, precision):
+    n, nc = 32, 2
+    rng = np.random.default_rng(3)
+    maps = synth.coil_maps(rng, n, n, nc)
+    x = synth.random_complex(rng, (n, n))
+    traj = synth.cartesian_trajectory(n, n)
+    with mr.Plan(n, n, nc, _dev(traj, torch.float32), precision) as plan:
+        got = mr.nudft_forward(plan, _dev(x), _dev(maps)).cpu().numpy()
+    ref = np.stack([np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(maps[c].astype(np.complex128) * x)))
+                    for c in range(nc)]).reshape(nc, -1)
+    assert _rel(got, ref) <= OP_TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_adjoint_identity_on_gpu(mr, precision):
+    nx, ny, nc = 96, 80, 6
+    maps, traj, x, y = _case(nx, ny, nc, 24, 160, seed=11)
+    with mr.Plan(nx, ny, nc, _dev(traj, torch.float32), precision) as plan:
+        dm = _dev(maps)
+        fx = mr.nudft_forward(plan, _dev(x), dm).cpu().numpy().astype(np.complex128)
+        fhy = mr.nudft_adjoint(plan, _dev(y), dm).cpu().numpy().astype(np.complex128)
+    lhs = np.vdot(fx, y)
+    rhs = np.vdot(x, fhy)
+    assert abs(lhs - rhs) <= 2 * OP_TOL[precision] * np.linalg.norm(fx) * np.linalg.norm(y)
+
+
+def test_tv_pair_and_threshold_match_oracle(mr):
+    rng = np.random.default_rng(5)
+    for nx, ny in [(33, 47), (128, 128), (1, 5)]:
+        x = synth.random_complex(rng, (nx, ny))
+        g = synth.random_complex(rng, (2, nx, ny))
+        gf = mr.tv_forward(_dev(x)).cpu().numpy()
+        ga = mr.tv_adjoint(_dev(g)).cpu().numpy()
+        ref_f = oracle.tv_forward(x)
+        ref_a = oracle.tv_adjoint(g)
+        assert np.abs(gf - ref_f).max() <= 4 * 2 ** -24 * 2 * np.abs(x).max()
+        assert np.abs(ga - ref_a).max() <= 4 * 2 ** -24 * 4 * np.abs(g).max()
+    a = synth.random_complex(rng, (5000,))
+    for t in (0.0, 0.3, 1.0, 5.0):
+        got = mr.soft_threshold(_dev(a), t).cpu().numpy()
+        ref = oracle.shrink(a.astype(np.complex128), np.float32(t))
+        assert np.abs(got - ref).max() <= 4 * 2 ** -24 * np.abs(a).max()
+
+
+def test_threshold_worked_values_eq9(mr):
+    import os
+    rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "eq9_soft_threshold.txt"), comments="#")
+    for a, lam, beta, expected in rows:
+        got = mr.soft_threshold(_dev(np.array([a + 0j])), lam / beta).cpu().numpy()[0]
+        assert abs(got.real - expected) <= 1e-6 * max(1.0, abs(expected)) and got.imag == 0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_degenerate_shapes(mr, precision):
+    # one pixel row, one coil, a single sample
+    for nx, ny, nc, nk in [(1, 1, 1, 1), (3, 17, 1, 5), (70, 1, 2, 33)]:
+        rng = np.random.default_rng(nx * 100 + ny)
+        maps = synth.random_complex(rng, (nc, nx, ny))
+        traj = rng.uniform(-0.5, 0.5, (nk, 2)).astype(np.float32)
+        x = synth.random_complex(rng, (nx, ny))
+        y = synth.random_complex(rng, (nc, nk))
+        with mr.Plan(nx, ny, nc, _dev(traj, torch.float32), precision) as plan:
+            dm = _dev(maps)
+            fwd = mr.nudft_forward(plan, _dev(x), dm).cpu().numpy()
+            adj = mr.nudft_adjoint(plan, _dev(y), dm).cpu().numpy()
+        assert _rel(fwd, oracle.forward(traj, x, maps)) <= OP_TOL[precision]
+        assert _rel(adj, oracle.adjoint(traj, y, maps)) <= OP_TOL[precision]
+
+
+def test_invalid_arguments_are_rejected(mr):
+    import ctypes
+    lib = mr.load()
+    h = ctypes.c_void_p()
+    traj = torch.zeros((4, 2), dtype=torch.float32, device="cuda")
+    assert lib.mri_plan_create(ctypes.byref(h), 0, 4, 4, 1, ctypes.c_void_p(traj.data_ptr()), 0, None) == \
+        mr.MRI_ERR_INVALID
+    assert lib.mri_plan_create(ctypes.byref(h), 4, 4, 4, 1, ctypes.c_void_p(traj.data_ptr()), 7, None) == \
+        mr.MRI_ERR_INVALID
+    assert b"precision" in lib.mri_last_error()
+    with mr.Plan(8, 8, 1, traj, "fp32") as plan:
+        with pytest.raises(mr.MriError) as ei:
+            mr.admm_reconstruct(plan, torch.zeros((1, 4), dtype=torch.complex64, device="cuda"),
+                                torch.zeros((1, 8, 8), dtype=torch.complex64, device="cuda"),
+                                lam=1e-3, beta=0.0, admm_iters=1, cg_iters=1)
+        assert ei.value.code == mr.MRI_ERR_INVALID
