@@ -112,18 +112,27 @@ static void timing_disarm(mri_plan *p, std::vector<std::pair<cudaEvent_t, cudaEv
     p->t_ev0 = p->t_ev1 = nullptr;
 }
 
-static cudaError_t op_forward(mri_plan *p, const float2 *image, const float2 *maps, float2 *out, int skip,
+// out[c * ld + k] = (F image)_c[k]
+static cudaError_t op_forward(mri_plan *p, const float2 *image, const float2 *maps, float2 *out, int ld, int skip,
                               cudaStream_t s) {
     const bool timed = timing_arm(p);
-    cudaError_t e = p->precision == MRI_BF16X3 ? launch_fwd_tc(p, image, maps, out, skip, s)
-                                               : launch_fwd_fp32(p, image, maps, out, skip, s);
+    cudaError_t e = p->precision == MRI_BF16X3 ? launch_fwd_tc(p, image, maps, out, ld, skip, s)
+                                               : launch_fwd_fp32(p, image, maps, out, ld, skip, s);
     if (timed) timing_disarm(p, p->ev_fwd);
     return e;
 }
 
+// Partial images of F^H kspace; kspace is [nc][nk] unless it is the plan's
+// own padded workspace y, into which any other input is copied first.
 static cudaError_t op_adjoint_partials(mri_plan *p, const float2 *kspace, int skip, cudaStream_t s) {
+    if (kspace != p->y) {
+        cudaError_t e = cudaMemcpy2DAsync(p->y, (size_t)p->nk_pad * sizeof(float2), kspace,
+                                          (size_t)p->nk * sizeof(float2), (size_t)p->nk * sizeof(float2), p->nc,
+                                          cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
     const bool timed = timing_arm(p);
-    cudaError_t e = p->precision == MRI_BF16X3 ? launch_adj_tc(p, kspace, skip, s) : launch_adj_fp32(p, kspace, skip, s);
+    cudaError_t e = p->precision == MRI_BF16X3 ? launch_adj_tc(p, skip, s) : launch_adj_fp32(p, skip, s);
     if (timed) timing_disarm(p, p->ev_adj);
     return e;
 }
@@ -131,7 +140,7 @@ static cudaError_t op_adjoint_partials(mri_plan *p, const float2 *kspace, int sk
 // out = F^H F src (+ half_beta Theta^H Theta src) (+ CG dot)
 static cudaError_t op_normal(mri_plan *p, const float2 *src, const float2 *maps, float2 *out, float half_beta,
                              bool cg_dot, int skip, cudaStream_t s) {
-    cudaError_t e = op_forward(p, src, maps, p->y, skip, s);
+    cudaError_t e = op_forward(p, src, maps, p->y, p->nk_pad, skip, s);
     if (e != cudaSuccess) return e;
     e = op_adjoint_partials(p, p->y, skip, s);
     if (e != cudaSuccess) return e;
@@ -183,6 +192,7 @@ MRI_API int mri_plan_create(mri_plan **out, int nx, int ny, int nk, int nc, cons
     p->ny_pad = round_up(ny, 16);
     p->kx = round_up(2 * nx, 64);
     p->kk = round_up(2 * nk, 64);
+    p->nk_pad = round_up(nk, 32);
 
     int rc = MRI_OK;
     const size_t npix = (size_t)nx * ny;
@@ -197,8 +207,8 @@ MRI_API int mri_plan_create(mri_plan **out, int nx, int ny, int nk, int nc, cons
             delete p;
             return fail(rc, "BF16x3 tensor-core path: shared-memory plan does not fit");
         }
-        if (rc == MRI_OK) rc = dev_alloc(p, &p->axT, (size_t)nx * nk);
-        if (rc == MRI_OK) rc = dev_alloc(p, &p->ayT, (size_t)ny * nk);
+        if (rc == MRI_OK) rc = dev_alloc(p, &p->axT, (size_t)nx * p->nk_pad);
+        if (rc == MRI_OK) rc = dev_alloc(p, &p->ayT, (size_t)ny * p->nk_pad);
         if (rc == MRI_OK) rc = dev_alloc(p, &p->afwd_hi, (size_t)2 * nk * p->kx);
         if (rc == MRI_OK) rc = dev_alloc(p, &p->afwd_lo, (size_t)2 * nk * p->kx);
         if (rc == MRI_OK) rc = dev_alloc(p, &p->badj_hi, (size_t)p->ny_pad * p->kk);
@@ -213,7 +223,7 @@ MRI_API int mri_plan_create(mri_plan **out, int nx, int ny, int nk, int nc, cons
         if (rc == MRI_OK) rc = dev_alloc(p, &p->ay, (size_t)nk * ny);
         if (rc == MRI_OK) rc = dev_alloc(p, &p->bsx, (size_t)nc * npix);
     }
-    if (rc == MRI_OK) rc = dev_alloc(p, &p->y, (size_t)nc * nk);
+    if (rc == MRI_OK) rc = dev_alloc(p, &p->y, (size_t)nc * p->nk_pad);
     if (rc == MRI_OK) rc = dev_alloc(p, &p->part, (size_t)p->ksplit * nc * ny * p->nx_pad);
     float2 **img_bufs[] = {&p->x, &p->xprev, &p->r, &p->d, &p->ad, &p->b, &p->fhd};
     for (float2 **q : img_bufs)
@@ -222,7 +232,7 @@ MRI_API int mri_plan_create(mri_plan **out, int nx, int ny, int nk, int nc, cons
     if (rc == MRI_OK) rc = dev_alloc(p, &p->eta, 2 * npix);
     // one slot pair per block of the largest reducing grid (element-wise
     // kernels use at most 1024 blocks, the adjoint reduction one per 32x32 tile)
-    p->partials_cap = 2 * std::max(1024, ceil_div(nx, 32) * ceil_div(ny, 32));
+    p->partials_cap = 2 * std::max(1024, ceil_div(nx, 32) * ny);
     if (rc == MRI_OK) rc = dev_alloc(p, &p->partials, (size_t)p->partials_cap);
     if (rc == MRI_OK) rc = dev_alloc(p, &p->scal, 1);
     if (rc != MRI_OK) {
@@ -238,6 +248,9 @@ MRI_API int mri_plan_create(mri_plan **out, int nx, int ny, int nk, int nc, cons
         for (int q = 0; q < 6 && e == cudaSuccess; ++q) e = cudaMemsetAsync(zb[q], 0, zn[q] * 2, s);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(p->part, 0, (size_t)p->ksplit * nc * ny * p->nx_pad * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->y, 0, (size_t)nc * p->nk_pad * 8, s);
+    if (e == cudaSuccess && p->axT) e = cudaMemsetAsync(p->axT, 0, (size_t)nx * p->nk_pad * 8, s);
+    if (e == cudaSuccess && p->ayT) e = cudaMemsetAsync(p->ayT, 0, (size_t)ny * p->nk_pad * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->scal, 0, sizeof(DevScalars), s);
     if (e == cudaSuccess && precision == MRI_BF16X3) {
         rc = tc_make_tensor_maps(p);
@@ -288,7 +301,7 @@ MRI_API size_t mri_plan_device_bytes(const mri_plan *p) { return p ? p->bytes : 
 MRI_API int mri_nudft_forward(mri_plan *p, const mri_c64 *image, const mri_c64 *maps, mri_c64 *kspace,
                               mri_stream_t stream) {
     if (!p || !image || !maps || !kspace) return fail(MRI_ERR_INVALID, "null argument");
-    cudaError_t e = op_forward(p, (const float2 *)image, (const float2 *)maps, (float2 *)kspace, kSkipNever,
+    cudaError_t e = op_forward(p, (const float2 *)image, (const float2 *)maps, (float2 *)kspace, p->nk, kSkipNever,
                                (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "forward operator");
     return MRI_OK;
@@ -383,7 +396,7 @@ MRI_API int mri_admm_reconstruct(mri_plan *p, const mri_c64 *kspace_in, const mr
         }
         KERNEL(launch_admm_dual(p, alpha_hist, m, s));  // Eq. 8 (dual), Alg. 4 relative change
         if (objective_hist) {
-            STEP(op_forward(p, p->x, maps, p->y, kSkipStep, s));
+            STEP(op_forward(p, p->x, maps, p->y, p->nk_pad, kSkipStep, s));
             KERNEL(launch_objective(p, kspace, prm->lambda, objective_hist, m, s));
         }
     }

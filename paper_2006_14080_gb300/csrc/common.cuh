@@ -73,14 +73,19 @@ __device__ __forceinline__ bool grid_reduce_last(const double (&part)[NV], doubl
     }
     __syncthreads();
     if (!is_last) return false;
+    __threadfence();
+    // every thread of the last block adds a fixed strided subset of the
+    // partials, then the block sums the per-thread values in a fixed order
+    __shared__ double scratch[32];
+    const int nthreads = blockDim.x * blockDim.y;
+    double s[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double v = 0.0;
+        for (int b = tid; b < nblocks; b += nthreads) v += __ldcg(&partials[(size_t)b * NV + q]);
+        s[q] = block_sum(v, scratch);
+    }
     if (tid == 0) {
-        __threadfence();
-        double s[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) s[q] = 0.0;
-        for (int b = 0; b < nblocks; ++b)
-#pragma unroll
-            for (int q = 0; q < NV; ++q) s[q] += __ldcg(&partials[(size_t)b * NV + q]);
         fin(s);
         *counter = 0u;
         __threadfence();

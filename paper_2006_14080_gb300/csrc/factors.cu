@@ -41,7 +41,7 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t &hi, uint3
 // cemb_hi/lo (nullable) receive the adjoint-product embedding of conj(F):
 // row idx, columns 2k, 2k+1 = (Re, -Im), leading dim ld_cemb.
 __global__ void factor_tile_kernel(const float *__restrict__ traj, int axis, int n, int nk,
-                                   float2 *__restrict__ F, float2 *__restrict__ FT,
+                                   float2 *__restrict__ F, float2 *__restrict__ FT, int ld_t,
                                    uint32_t *__restrict__ emb_hi, uint32_t *__restrict__ emb_lo, int ld_emb,
                                    uint32_t *__restrict__ cemb_hi, uint32_t *__restrict__ cemb_lo,
                                    int ld_cemb) {
@@ -75,7 +75,7 @@ __global__ void factor_tile_kernel(const float *__restrict__ traj, int axis, int
         const int idx = p0 + q, k = k0 + tx;
         if (k < nk && idx < n) {
             const float2 v = tile[tx][q];
-            if (FT) FT[(size_t)idx * nk + k] = v;
+            if (FT) FT[(size_t)idx * ld_t + k] = v;
             if (cemb_hi) {
                 uint32_t h, l;
                 // conj(F) = (Re, -Im) at columns 2k, 2k+1
@@ -93,14 +93,15 @@ cudaError_t launch_factors(mri_plan *p, const float *traj, cudaStream_t s) {
     dim3 block(32, 8);
     {
         dim3 grid(ceil_div(p->nk, 32), ceil_div(p->nx, 32));
-        factor_tile_kernel<<<grid, block, 0, s>>>(traj, 0, p->nx, p->nk, p->ax, p->axT,
+        factor_tile_kernel<<<grid, block, 0, s>>>(traj, 0, p->nx, p->nk, p->ax, p->axT, p->nk_pad,
                                                   (uint32_t *)p->afwd_hi, (uint32_t *)p->afwd_lo, p->kx,
                                                   nullptr, nullptr, 0);
     }
     {
         dim3 grid(ceil_div(p->nk, 32), ceil_div(p->ny, 32));
-        factor_tile_kernel<<<grid, block, 0, s>>>(traj, 1, p->ny, p->nk, p->ay, p->ayT, nullptr, nullptr, 0,
-                                                  (uint32_t *)p->badj_hi, (uint32_t *)p->badj_lo, p->kk);
+        factor_tile_kernel<<<grid, block, 0, s>>>(traj, 1, p->ny, p->nk, p->ay, p->ayT, p->nk_pad, nullptr,
+                                                  nullptr, 0, (uint32_t *)p->badj_hi, (uint32_t *)p->badj_lo,
+                                                  p->kk);
     }
     return cudaGetLastError();
 }

@@ -64,6 +64,8 @@ struct mri_plan {
     float2 *axT = nullptr;  // [nx][nk]
     float2 *ayT = nullptr;  // [ny][nk]
 
+    int nk_pad = 0;   // round_up(nk, 32): leading dimension of sample-indexed rows (axT, ayT, y)
+
     // BF16 hi/lo real-embedded operands (tensor-core path)
     int kx = 0;       // round_up(2*nx, 64): K of the forward product
     int kk = 0;       // round_up(2*nk, 64): K of the adjoint product
@@ -75,10 +77,11 @@ struct mri_plan {
     __nv_bfloat16 *badj_hi = nullptr, *badj_lo = nullptr;  // [ny_pad][kk]
     __nv_bfloat16 *bfwd_hi = nullptr, *bfwd_lo = nullptr;  // [nc*ny_pad][kx]
     CUtensorMap tm_afwd_hi, tm_afwd_lo, tm_bfwd_hi, tm_bfwd_lo, tm_badj_hi, tm_badj_lo;
+    CUtensorMap tm_axT, tm_y, tm_ayT;  // FP32 views of axT, y, ayT for staged factor tiles
 
     // operator workspace
     float2 *bsx = nullptr;    // [nc][nx][ny] S_c . x (FP32 path)
-    float2 *y = nullptr;      // [nc][nk]
+    float2 *y = nullptr;      // [nc][nk_pad] k-space workspace (padding stays zero)
     float2 *part = nullptr;   // [ksplit][nc][ny][nx_pad] adjoint partial images
     int ksplit = 1;           // k-space splits of the adjoint product
     int ksplit_blocks = 0;    // K blocks per split (tensor path) or samples per split (FP32)
@@ -117,18 +120,18 @@ void set_error(const std::string &msg);
 // factors.cu
 cudaError_t launch_factors(mri_plan *p, const float *traj, cudaStream_t s);
 
-// nudft_fp32.cu
-cudaError_t launch_fwd_fp32(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace,
+// nudft_fp32.cu -- forward writes kspace[c * ld + k]; adjoint reads p->y
+cudaError_t launch_fwd_fp32(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace, int ld,
                             int skip, cudaStream_t s);
-cudaError_t launch_adj_fp32(mri_plan *p, const float2 *kspace, int skip, cudaStream_t s);
+cudaError_t launch_adj_fp32(mri_plan *p, int skip, cudaStream_t s);
 
-// nudft_tc.cu
+// nudft_tc.cu -- same conventions
 bool tc_supported(const mri_plan *p, std::string *why);
 int tc_plan_tiling(mri_plan *p);       // tile shapes and k-space splits; MRI_* status
 int tc_make_tensor_maps(mri_plan *p);  // TMA descriptors of the allocated operands; MRI_* status
-cudaError_t launch_fwd_tc(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace,
+cudaError_t launch_fwd_tc(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace, int ld,
                           int skip, cudaStream_t s);
-cudaError_t launch_adj_tc(mri_plan *p, const float2 *kspace, int skip, cudaStream_t s);
+cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s);
 
 // solver.cu
 struct ReduceEpilogue {

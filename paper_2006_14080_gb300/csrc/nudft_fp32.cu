@@ -34,7 +34,8 @@ __global__ void coil_product_kernel(const float2 *__restrict__ x, const float2 *
 
 __global__ void __launch_bounds__(256) fwd_fp32_kernel(const float2 *__restrict__ ax, const float2 *__restrict__ ay,
                                                        const float2 *__restrict__ bsx, float2 *__restrict__ y,
-                                                       int nx, int ny, int nk, const DevScalars *sc, int skip) {
+                                                       int y_ld, int nx, int ny, int nk, const DevScalars *sc,
+                                                       int skip) {
     if (should_skip(sc, skip)) return;
     __shared__ __align__(16) float2 As[2][BK][BM];  // As[k][m] = A_x[k0+m][i0+k]
     __shared__ __align__(16) float2 Bs[2][BK][BN];  // Bs[k][n] = B_c[i0+k][j0+n]
@@ -132,14 +133,14 @@ __global__ void __launch_bounds__(256) fwd_fp32_kernel(const float2 *__restrict_
             im += __shfl_xor_sync(0xffffffffu, im, o);
         }
         const int kk = k0 + ty * 4 + m;
-        if (tx == 0 && kk < nk) y[(size_t)c * nk + kk] = make_float2(re, im);
+        if (tx == 0 && kk < nk) y[(size_t)c * y_ld + kk] = make_float2(re, im);
     }
 }
 
 // part[p][c][j][i] = sum_{k in split p} conj(A_x[k][i]) y_c[k] conj(A_y[k][j])
 __global__ void __launch_bounds__(256) adj_fp32_kernel(const float2 *__restrict__ ax, const float2 *__restrict__ ay,
                                                        const float2 *__restrict__ y, float2 *__restrict__ part,
-                                                       int nx, int ny, int nk, int nc, int nx_pad,
+                                                       int y_ld, int nx, int ny, int nk, int nc, int nx_pad,
                                                        int samples_per_split, const DevScalars *sc, int skip) {
     if (should_skip(sc, skip)) return;
     __shared__ __align__(16) float2 Us[2][BK][BM];  // Us[k][m] = conj(A_x[k][i0+m]) y_c[k]
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(256) adj_fp32_kernel(const float2 *__restrict_
     const int c = blockIdx.y, p = blockIdx.z;
     const int kbeg = p * samples_per_split;
     const int kend = min(nk, kbeg + samples_per_split);
-    const float2 *yc = y + (size_t)c * nk;
+    const float2 *yc = y + (size_t)c * y_ld;
 
     float2 acc[4][4];
 #pragma unroll
@@ -230,23 +231,23 @@ __global__ void __launch_bounds__(256) adj_fp32_kernel(const float2 *__restrict_
 
 }  // namespace
 
-cudaError_t launch_fwd_fp32(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace, int skip,
-                            cudaStream_t s) {
+cudaError_t launch_fwd_fp32(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace, int ld,
+                            int skip, cudaStream_t s) {
     const int npix = p->nx * p->ny;
     coil_product_kernel<<<ceil_div(npix, 256), 256, 0, s>>>(image, maps, p->bsx, npix, p->nc, p->scal, skip);
     dim3 grid(ceil_div(p->nk, BM), p->nc);
     timing_begin(p, s);
-    fwd_fp32_kernel<<<grid, 256, 0, s>>>(p->ax, p->ay, p->bsx, kspace, p->nx, p->ny, p->nk, p->scal, skip);
+    fwd_fp32_kernel<<<grid, 256, 0, s>>>(p->ax, p->ay, p->bsx, kspace, ld, p->nx, p->ny, p->nk, p->scal, skip);
     timing_end(p, s);
     p->launches += 2;
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_fp32(mri_plan *p, const float2 *kspace, int skip, cudaStream_t s) {
+cudaError_t launch_adj_fp32(mri_plan *p, int skip, cudaStream_t s) {
     dim3 grid(ceil_div(p->nx, BM) * ceil_div(p->ny, BN), p->nc, p->ksplit);
     timing_begin(p, s);
-    adj_fp32_kernel<<<grid, 256, 0, s>>>(p->ax, p->ay, kspace, p->part, p->nx, p->ny, p->nk, p->nc, p->nx_pad,
-                                         p->ksplit_blocks, p->scal, skip);
+    adj_fp32_kernel<<<grid, 256, 0, s>>>(p->ax, p->ay, p->y, p->part, p->nk_pad, p->nx, p->ny, p->nk, p->nc,
+                                         p->nx_pad, p->ksplit_blocks, p->scal, skip);
     timing_end(p, s);
     p->launches += 1;
     return cudaGetLastError();

@@ -11,21 +11,24 @@
 // Forward  (Eq. 1):  Z = A_x (S_c . X) for all coils at once
 //     A  = embedded A_x          [2 nk][kx]        static, TMA
 //     B  = (S_c . X)^T per coil  [nc * ny_pad][kx] written by fwd_operand_kernel, TMA
-//   tile: 128 rows (64 samples) x block_n columns (whole coils); the epilogue
-//   forms y_c[k] = sum_j Z[k][j] A_y[k][j] from TMEM and writes y.
+//   tile: 128 rows (64 samples) x block_n columns (whole coils).  The
+//   epilogue forms y_c[k] = sum_j Z[k][j] A_y[k][j] from TMEM, with the
+//   matching 64-sample x 32-column tiles of A_y staged in shared memory by a
+//   TMA warp.
 // Adjoint: W_c = U_c conj(A_y) with U_c[i][k] = conj(A_x[k][i]) y_c[k]
-//     A  = embedded U_c          built in shared memory by producer warps
+//     A  = embedded U_c          built in shared memory by producer warps from
+//                                A_x^H and y tiles that a TMA warp stages
 //     B  = conj(A_y)^T           [ny_pad][kk]      static, TMA
 //   tile: 128 rows (64 pixels of one coil) x ny_pad columns, split over
 //   contiguous k-space ranges; the epilogue writes partial images that
 //   launch_adj_reduce sums in a fixed order (the paper's cross-core sum).
 //
-// Both kernels are persistent (one CTA per SM), warp-specialised, with a
-// multi-stage mbarrier ring between the operand producers and the single
-// UMMA-issuing thread and a double-buffered TMEM accumulator between the
-// UMMA thread and the epilogue warps.  Every wait is bounded: on give-up the
-// block raises a shared abort flag, drains its own copies and UMMAs, frees
-// TMEM, records kStatusTimeout and returns.
+// Both kernels are persistent (one CTA per SM), warp-specialised, with
+// mbarrier rings between the loaders/producers and the single UMMA-issuing
+// thread and a double-buffered TMEM accumulator between the UMMA thread and
+// the epilogue warps.  Every wait is bounded: on give-up the block raises a
+// shared abort flag, drains its own copies and UMMAs, frees TMEM, records
+// kStatusTimeout and returns.
 #include <algorithm>
 #include <string>
 
@@ -42,14 +45,18 @@ using namespace tc;
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s per wait
 constexpr uint64_t kDrainLimitNs = 200000000ull;  // 0.2 s per drain wait
 constexpr int kTileBytesA = kTcBlockM * 128;      // 128 rows x 64 bf16
-constexpr int kFwdThreads = 192;                  // w0 TMA, w1 UMMA, w2-5 epilogue
-constexpr int kAdjThreads = 288;                  // w0-3 producers (+TMA), w4 UMMA, w5-8 epilogue
+constexpr int kAyChunkBytes = 32 * 64 * 8;        // 32 columns x 64 samples, complex FP32
+constexpr int kRawBytes = 2 * 64 * 128;           // 64 pixels x 32 samples of A_x^H, complex FP32
+constexpr int kRawYBytes = 32 * 8;                // 32 samples of y_c
+constexpr int kFwdThreads = 224;                  // w0 TMA, w1 UMMA, w2 A_y TMA, w3-6 epilogue
+constexpr int kAdjThreads = 320;                  // w0-3 producers, w4 UMMA, w5-8 epilogue, w9 TMA
 constexpr int kMaxSmem = 227 * 1024;
+constexpr int kSmemSlack = 1024 + 256;            // alignment + barriers
+constexpr int kMaxCoilsPerTile = 16;
 
 struct FwdParams {
-    const float2 *ayT;  // [ny][nk]
-    float2 *y;          // [nc][nk]
-    int nk, ny, ny_pad, nc, cpt, block_n, n_tiles, num_tiles, num_kb, stages;
+    float2 *y;  // [nc][y_ld]
+    int y_ld, nk, ny_pad, nc, cpt, block_n, n_tiles, num_tiles, num_kb, stages, ay_stages;
     uint32_t tmem_cols;
     const DevScalars *sc;
     int skip;
@@ -57,10 +64,9 @@ struct FwdParams {
 };
 
 struct AdjParams {
-    const float2 *axT;  // [nx][nk]
-    const float2 *y;    // [nc][nk]
-    float2 *part;       // [ksplit][nc][ny][nx_pad]
-    int nx, nk, ny, ny_pad, nx_pad, nc, tiles_per_coil, m_tiles, kb_per_split, num_kb, num_units, stages;
+    float2 *part;  // [ksplit][nc][ny][nx_pad]
+    int nx, ny, ny_pad, nx_pad, nc, tiles_per_coil, m_tiles, kb_per_split, num_kb, num_units;
+    int stages, raw_stages;
     uint32_t tmem_cols;
     const DevScalars *sc;
     int skip;
@@ -78,54 +84,70 @@ __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity) {
     mbar_wait(bar, parity, &local, kDrainLimitNs);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
-    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
-           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t *>(&v); }
+
+// hi/lo split of a pair of FP32 values into packed bf16x2 words (a in the low half).
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat162 h = __float22bfloat162_rn(make_float2(a, b));
+    const float2 hf = __bfloat1622float2(h);
+    hi = bf2_bits(h);
+    lo = bf2_bits(__float22bfloat162_rn(make_float2(a - hf.x, b - hf.y)));
 }
 
-// hi/lo split of a pair of FP32 values into packed bf16x2 words.
-__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo) {
-    const __nv_bfloat16 ah = __float2bfloat16_rn(a), bh = __float2bfloat16_rn(b);
-    hi = (uint32_t)__bfloat16_as_ushort(ah) | ((uint32_t)__bfloat16_as_ushort(bh) << 16);
-    lo = pack_bf16x2(a - __bfloat162float(ah), b - __bfloat162float(bh));
+// For U = (ur, ui): the Re-row word (ur, -ui) and the Im-row word (ui, ur) of
+// the real embedding, hi and lo.  Negation and swapping are exact in bf16, so
+// the four words come from one split of (ur, ui).
+__device__ __forceinline__ void split_embed(float2 u, uint32_t &hre, uint32_t &lre, uint32_t &him, uint32_t &lim) {
+    uint32_t h, l;
+    split2(u.x, u.y, h, l);
+    hre = h ^ 0x80000000u;
+    lre = l ^ 0x80000000u;
+    him = __byte_perm(h, 0, 0x1032);
+    lim = __byte_perm(l, 0, 0x1032);
 }
+
+// Ring position: stage index and phase bit advance together.
+struct Ring {
+    int stage = 0;
+    uint32_t phase = 0;
+    __device__ __forceinline__ void next(int n) {
+        if (++stage == n) {
+            stage = 0;
+            phase ^= 1u;
+        }
+    }
+};
 
 // ---------------------------------------------------------------------------
 // Forward operand: B[(c*ny_pad + j)][2i + {0,1}] = split(Re, Im of S_c[i][j] x[i][j])
-// block (32, 8) over a 32 x 32 (i, j) tile, transposed through shared memory.
+// block (32, 8) over a 32 x 32 (i, j) tile of coil blockIdx.z, transposed
+// through shared memory.
 __global__ void fwd_operand_kernel(const float2 *__restrict__ x, const float2 *__restrict__ maps,
                                    uint32_t *__restrict__ hi, uint32_t *__restrict__ lo, int nx, int ny, int ny_pad,
-                                   int kx, int nc, const DevScalars *sc, int skip) {
+                                   int kx, const DevScalars *sc, int skip) {
     if (should_skip(sc, skip)) return;
-    __shared__ float2 xs[32][33];
-    __shared__ float2 ss[32][33];
+    __shared__ float2 ts[32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32, c = blockIdx.z;
     const size_t npix = (size_t)nx * ny;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int i = i0 + ty + 8 * q, j = j0 + tx;
-        xs[ty + 8 * q][tx] = (i < nx && j < ny) ? x[(size_t)i * ny + j] : make_float2(0.f, 0.f);
+        ts[ty + 8 * q][tx] = (i < nx && j < ny)
+                                 ? cmul(maps[c * npix + (size_t)i * ny + j], x[(size_t)i * ny + j])
+                                 : make_float2(0.f, 0.f);
     }
-    for (int c = 0; c < nc; ++c) {
-        __syncthreads();
+    __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = i0 + ty + 8 * q, j = j0 + tx;
-            ss[ty + 8 * q][tx] = (i < nx && j < ny) ? maps[c * npix + (size_t)i * ny + j] : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int j = j0 + ty + 8 * q, i = i0 + tx;
-            if (i < nx && j < ny) {
-                const float2 v = cmul(ss[tx][ty + 8 * q], xs[tx][ty + 8 * q]);
-                uint32_t h, l;
-                split2(v.x, v.y, h, l);
-                const size_t off = ((size_t)c * ny_pad + j) * (kx / 2) + i;
-                hi[off] = h;
-                lo[off] = l;
-            }
+    for (int q = 0; q < 4; ++q) {
+        const int j = j0 + ty + 8 * q, i = i0 + tx;
+        if (i < nx && j < ny) {
+            const float2 v = ts[tx][ty + 8 * q];
+            uint32_t h, l;
+            split2(v.x, v.y, h, l);
+            const size_t off = ((size_t)c * ny_pad + j) * (kx / 2) + i;
+            hi[off] = h;
+            lo[off] = l;
         }
     }
 }
@@ -134,25 +156,32 @@ __global__ void fwd_operand_kernel(const float2 *__restrict__ x, const float2 *_
 __global__ void __launch_bounds__(kFwdThreads, 1)
     fwd_tc_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
                   const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
-                  const FwdParams P) {
+                  const __grid_constant__ CUtensorMap t_ay, const FwdParams P) {
     if (should_skip(P.sc, P.skip)) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     const uint32_t b_bytes = (uint32_t)P.block_n * 128u;
     const uint32_t stage_bytes = 2u * kTileBytesA + 2u * b_bytes;
-    const int S = P.stages;
-    uint64_t *bars = (uint64_t *)(smem + (size_t)S * stage_bytes);
+    const int S = P.stages, R = P.ay_stages;
+    uint8_t *ay_ring = smem + (size_t)S * stage_bytes;
+    uint64_t *bars = (uint64_t *)(ay_ring + (size_t)R * kAyChunkBytes);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + S);
-    const uint32_t tfull0 = smem_u32(bars + 2 * S), tempty0 = smem_u32(bars + 2 * S + 2);
-    const uint32_t fin = smem_u32(bars + 2 * S + 4);
-    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * S + 5);
+    const uint32_t yfull0 = smem_u32(bars + 2 * S), yempty0 = smem_u32(bars + 2 * S + R);
+    const uint32_t tfull0 = smem_u32(bars + 2 * S + 2 * R), tempty0 = smem_u32(bars + 2 * S + 2 * R + 2);
+    const uint32_t fin = smem_u32(bars + 2 * S + 2 * R + 4);
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * S + 2 * R + 5);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_jc = (P.ny_pad + 31) / 32;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int r = 0; r < R; ++r) {
+            mbar_init(yfull0 + 8 * r, 1);
+            mbar_init(yempty0 + 8 * r, 128);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull0 + 8 * a, 1);
@@ -171,6 +200,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         prefetch_tensormap(&ta_lo);
         prefetch_tensormap(&tb_hi);
         prefetch_tensormap(&tb_lo);
+        prefetch_tensormap(&t_ay);
     }
     fence_before_sync();
     __syncthreads();
@@ -178,28 +208,25 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     const uint32_t tmem_base = *tmem_slot;
 
     if (warp == 0) {
+        // operand loader
         if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
+            Ring rg;
             uint32_t issued_phase[4] = {0, 0, 0, 0};
             int issued_mask = 0;
             for (int tile = blockIdx.x; tile < P.num_tiles && !*abort_flag; tile += gridDim.x) {
                 const int m_blk = tile / P.n_tiles, n_blk = tile % P.n_tiles;
                 for (int kb = 0; kb < P.num_kb; ++kb) {
-                    if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, kWaitLimitNs)) break;
-                    const uint32_t sbase = smem_u32(smem + (size_t)stage * stage_bytes);
-                    const uint32_t fb = full0 + 8 * stage;
+                    if (!mbar_wait(empty0 + 8 * rg.stage, rg.phase ^ 1, abort_flag, kWaitLimitNs)) break;
+                    const uint32_t sbase = smem_u32(smem + (size_t)rg.stage * stage_bytes);
+                    const uint32_t fb = full0 + 8 * rg.stage;
                     mbar_arrive_expect_tx(fb, stage_bytes);
                     tma_load_2d(sbase, &ta_hi, fb, kb * kTcBlockK, m_blk * kTcBlockM);
                     tma_load_2d(sbase + kTileBytesA, &ta_lo, fb, kb * kTcBlockK, m_blk * kTcBlockM);
                     tma_load_2d(sbase + 2 * kTileBytesA, &tb_hi, fb, kb * kTcBlockK, n_blk * P.block_n);
                     tma_load_2d(sbase + 2 * kTileBytesA + b_bytes, &tb_lo, fb, kb * kTcBlockK, n_blk * P.block_n);
-                    issued_phase[stage] = phase;
-                    issued_mask |= 1 << stage;
-                    if (++stage == S) {
-                        stage = 0;
-                        phase ^= 1;
-                    }
+                    issued_phase[rg.stage] = rg.phase;
+                    issued_mask |= 1 << rg.stage;
+                    rg.next(S);
                 }
             }
             if (*abort_flag)
@@ -207,10 +234,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                     if (issued_mask & (1 << s)) drain_wait(full0 + 8 * s, issued_phase[s]);
         }
     } else if (warp == 1) {
+        // UMMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32(kTcBlockM, P.block_n);
-            int stage = 0;
-            uint32_t phase = 0;
+            Ring rg;
             int lt = 0;
             bool issued_any = false;
             for (int tile = blockIdx.x; tile < P.num_tiles; tile += gridDim.x, ++lt) {
@@ -221,12 +248,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                 const uint32_t d_tmem = tmem_base + (uint32_t)(a * P.block_n);
                 bool ok = true;
                 for (int kb = 0; kb < P.num_kb; ++kb) {
-                    if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, kWaitLimitNs)) {
+                    if (!mbar_wait(full0 + 8 * rg.stage, rg.phase, abort_flag, kWaitLimitNs)) {
                         ok = false;
                         break;
                     }
                     fence_after_sync();
-                    const uint32_t sa_hi = smem_u32(smem + (size_t)stage * stage_bytes);
+                    const uint32_t sa_hi = smem_u32(smem + (size_t)rg.stage * stage_bytes);
                     const uint32_t sa_lo = sa_hi + kTileBytesA;
                     const uint32_t sb_hi = sa_hi + 2 * kTileBytesA;
                     const uint32_t sb_lo = sb_hi + b_bytes;
@@ -240,11 +267,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                         umma_f16(d_tmem, dal, dbh, idesc, 1u);
                     }
                     issued_any = true;
-                    umma_commit(empty0 + 8 * stage);
-                    if (++stage == S) {
-                        stage = 0;
-                        phase ^= 1;
-                    }
+                    umma_commit(empty0 + 8 * rg.stage);
+                    rg.next(S);
                 }
                 if (!ok) break;
                 umma_commit(tfull0 + 8 * a);
@@ -254,12 +278,36 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                 drain_wait(fin, 0);
             }
         }
+    } else if (warp == 2) {
+        // A_y tile loader: for each tile, the 64-sample x 32-column chunks in column order
+        if (lane == 0) {
+            Ring rg;
+            uint32_t issued_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            int issued_mask = 0;
+            for (int tile = blockIdx.x; tile < P.num_tiles && !*abort_flag; tile += gridDim.x) {
+                const int m_blk = tile / P.n_tiles;
+                for (int jc = 0; jc < n_jc; ++jc) {
+                    if (!mbar_wait(yempty0 + 8 * rg.stage, rg.phase ^ 1, abort_flag, kWaitLimitNs)) break;
+                    const uint32_t yb = yfull0 + 8 * rg.stage;
+                    mbar_arrive_expect_tx(yb, kAyChunkBytes);
+                    tma_load_2d(smem_u32(ay_ring + (size_t)rg.stage * kAyChunkBytes), &t_ay, yb,
+                                m_blk * (kTcBlockM), jc * 32);
+                    issued_phase[rg.stage] = rg.phase;
+                    issued_mask |= 1 << rg.stage;
+                    rg.next(R);
+                }
+            }
+            if (*abort_flag)
+                for (int r = 0; r < R; ++r)
+                    if (issued_mask & (1 << r)) drain_wait(yfull0 + 8 * r, issued_phase[r]);
+        }
     } else {
         // epilogue: warp (w % 4) reads TMEM lanes [32 (w % 4), 32 (w % 4) + 32)
         const int wq = warp & 3;
         const int row = wq * 32 + lane;
-        const int o = row & 1;
+        const int o = row & 1, kk_local = row >> 1;
         const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
+        Ring yr;
         int lt = 0;
         for (int tile = blockIdx.x; tile < P.num_tiles; tile += gridDim.x, ++lt) {
             const int a = lt & 1;
@@ -267,52 +315,60 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             if (!mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) break;
             fence_after_sync();
             const int m_blk = tile / P.n_tiles, n_blk = tile % P.n_tiles;
-            const int kappa = m_blk * (kTcBlockM / 2) + (row >> 1);
-            const bool kv = kappa < P.nk;
-            for (int cs = 0; cs < P.cpt; ++cs) {
-                const int c = n_blk * P.cpt + cs;
-                if (c >= P.nc) break;
-                const uint32_t col0 = (uint32_t)(a * P.block_n + cs * P.ny_pad);
-                float s0 = 0.f, s1 = 0.f;
-                int jc = 0;
-                for (; jc + 32 <= P.ny_pad; jc += 32) {
-                    float v[32];
-                    tmem_ld_32cols(tmem_base + lane_base + col0 + jc, v);
-                    if (kv) {
+            float s0[kMaxCoilsPerTile], s1[kMaxCoilsPerTile];
 #pragma unroll
-                        for (int q = 0; q < 32; ++q) {
-                            const int j = jc + q;
-                            if (j < P.ny) {
-                                const float2 ay = __ldg(&P.ayT[(size_t)j * P.nk + kappa]);
-                                const float c0 = o ? -ay.y : ay.x, c1 = o ? ay.x : ay.y;
-                                s0 = fmaf(v[q], c0, s0);
-                                s1 = fmaf(v[q], c1, s1);
+            for (int cs = 0; cs < kMaxCoilsPerTile; ++cs) s0[cs] = s1[cs] = 0.f;
+            bool ok = true;
+            for (int jc = 0; jc < n_jc; ++jc) {
+                if (!mbar_wait(yfull0 + 8 * yr.stage, yr.phase, abort_flag, kWaitLimitNs)) {
+                    ok = false;
+                    break;
+                }
+                // A_y[k][j] of this thread's sample at column j = 32 jc + q: smem [q][k_local]
+                const float2 *ay = reinterpret_cast<const float2 *>(ay_ring + (size_t)yr.stage * kAyChunkBytes) +
+                                   kk_local;
+                const bool full32 = P.ny_pad - 32 * jc >= 32;
+#pragma unroll
+                for (int cs = 0; cs < kMaxCoilsPerTile; ++cs) {
+                    if (cs < P.cpt) {
+                        const uint32_t col = (uint32_t)(a * P.block_n + cs * P.ny_pad + 32 * jc);
+                        if (full32) {
+                            float v[32];
+                            tmem_ld_32cols(tmem_base + lane_base + col, v);
+#pragma unroll
+                            for (int q = 0; q < 32; ++q) {
+                                const float2 w = ay[q * 64];
+                                s0[cs] = fmaf(v[q], o ? -w.y : w.x, s0[cs]);
+                                s1[cs] = fmaf(v[q], o ? w.x : w.y, s1[cs]);
+                            }
+                        } else {
+                            float v[16];
+                            tmem_ld_16cols(tmem_base + lane_base + col, v);
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) {
+                                const float2 w = ay[q * 64];
+                                s0[cs] = fmaf(v[q], o ? -w.y : w.x, s0[cs]);
+                                s1[cs] = fmaf(v[q], o ? w.x : w.y, s1[cs]);
                             }
                         }
                     }
                 }
-                if (jc < P.ny_pad) {  // 16-column tail
-                    float v[16];
-                    tmem_ld_16cols(tmem_base + lane_base + col0 + jc, v);
-                    if (kv) {
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) {
-                            const int j = jc + q;
-                            if (j < P.ny) {
-                                const float2 ay = __ldg(&P.ayT[(size_t)j * P.nk + kappa]);
-                                const float c0 = o ? -ay.y : ay.x, c1 = o ? ay.x : ay.y;
-                                s0 = fmaf(v[q], c0, s0);
-                                s1 = fmaf(v[q], c1, s1);
-                            }
-                        }
-                    }
-                }
-                s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-                s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-                if (o == 0 && kv) P.y[(size_t)c * P.nk + kappa] = make_float2(s0, s1);
+                mbar_arrive(yempty0 + 8 * yr.stage);
+                yr.next(R);
             }
             fence_before_sync();
             mbar_arrive(tempty0 + 8 * a);
+            if (!ok) break;
+            const int kappa = m_blk * (kTcBlockM / 2) + kk_local;
+#pragma unroll
+            for (int cs = 0; cs < kMaxCoilsPerTile; ++cs) {
+                if (cs < P.cpt) {
+                    const float r0 = s0[cs] + __shfl_xor_sync(0xffffffffu, s0[cs], 1);
+                    const float r1 = s1[cs] + __shfl_xor_sync(0xffffffffu, s1[cs], 1);
+                    const int c = n_blk * P.cpt + cs;
+                    if (o == 0 && kappa < P.nk && c < P.nc) P.y[(size_t)c * P.y_ld + kappa] = make_float2(r0, r1);
+                }
+            }
         }
     }
 
@@ -328,25 +384,33 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kAdjThreads, 1)
     adj_tc_kernel(const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
+                  const __grid_constant__ CUtensorMap t_axT, const __grid_constant__ CUtensorMap t_y,
                   const AdjParams P) {
     if (should_skip(P.sc, P.skip)) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     const uint32_t b_bytes = (uint32_t)P.ny_pad * 128u;
     const uint32_t stage_bytes = 2u * kTileBytesA + 2u * b_bytes;
-    const int S = P.stages;
-    uint64_t *bars = (uint64_t *)(smem + (size_t)S * stage_bytes);
+    const int S = P.stages, R = P.raw_stages;
+    uint8_t *raw = smem + (size_t)S * stage_bytes;
+    uint8_t *yraw = raw + (size_t)R * kRawBytes;
+    uint64_t *bars = (uint64_t *)(yraw + (size_t)R * kRawYBytes);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + S);
-    const uint32_t tfull0 = smem_u32(bars + 2 * S), tempty0 = smem_u32(bars + 2 * S + 2);
-    const uint32_t fin = smem_u32(bars + 2 * S + 4);
-    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * S + 5);
+    const uint32_t rfull0 = smem_u32(bars + 2 * S), rempty0 = smem_u32(bars + 2 * S + R);
+    const uint32_t tfull0 = smem_u32(bars + 2 * S + 2 * R), tempty0 = smem_u32(bars + 2 * S + 2 * R + 2);
+    const uint32_t fin = smem_u32(bars + 2 * S + 2 * R + 4);
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * S + 2 * R + 5);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(full0 + 8 * s, 129);  // 128 producer threads + the TMA expect_tx arrival
+            mbar_init(full0 + 8 * s, 129);  // 128 producer threads + the B loads' expect_tx arrival
             mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int r = 0; r < R; ++r) {
+            mbar_init(rfull0 + 8 * r, 1);
+            mbar_init(rempty0 + 8 * r, 128);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull0 + 8 * a, 1);
@@ -360,9 +424,11 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         tmem_alloc(smem_u32(tmem_slot), P.tmem_cols);
         tmem_relinquish();
     }
-    if (threadIdx.x == 0) {
+    if (warp == 9 && lane == 0) {
         prefetch_tensormap(&tb_hi);
         prefetch_tensormap(&tb_lo);
+        prefetch_tensormap(&t_axT);
+        prefetch_tensormap(&t_y);
     }
     fence_before_sync();
     __syncthreads();
@@ -370,82 +436,69 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
     const uint32_t tmem_base = *tmem_slot;
 
     if (warp < 4) {
-        // producers: thread t builds row (ii = t/2, o = t%2) of the embedded U tile
+        // producers: thread t builds, for pixel ii = t/2 and samples [16h, 16h+16)
+        // of the K block (h = t%2), the Re row 2ii and the Im row 2ii+1 of U
         const int t = threadIdx.x;
-        const int ii = t >> 1, o = t & 1;
-        int stage = 0;
-        uint32_t phase = 0;
+        const int ii = t >> 1, h = t & 1;
+        Ring rr, rs;
         uint32_t issued_phase[4] = {0, 0, 0, 0};
         int issued_mask = 0;
         for (int u = blockIdx.x; u < P.num_units && !*abort_flag; u += gridDim.x) {
-            const int p = u / P.m_tiles, m = u % P.m_tiles;
-            const int c = m / P.tiles_per_coil, ib = m % P.tiles_per_coil;
-            const int i = ib * 64 + ii;
-            const bool iv = i < P.nx;
+            const int p = u / P.m_tiles;
             const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
-            const float2 *arow = P.axT + (size_t)(iv ? i : 0) * P.nk;
-            const float2 *yc = P.y + (size_t)c * P.nk;
             bool ok = true;
             for (int kb = kb0; kb < kb1; ++kb) {
-                if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, kWaitLimitNs)) {
+                if (!mbar_wait(rfull0 + 8 * rr.stage, rr.phase, abort_flag, kWaitLimitNs) ||
+                    !mbar_wait(empty0 + 8 * rs.stage, rs.phase ^ 1, abort_flag, kWaitLimitNs)) {
                     ok = false;
                     break;
                 }
-                uint8_t *sbase = smem + (size_t)stage * stage_bytes;
-                const uint32_t fb = full0 + 8 * stage;
+                uint8_t *sbase = smem + (size_t)rs.stage * stage_bytes;
+                const uint32_t fb = full0 + 8 * rs.stage;
                 if (t == 0) {
                     const uint32_t sb = smem_u32(sbase + 2 * kTileBytesA);
                     mbar_arrive_expect_tx(fb, 2u * b_bytes);
                     tma_load_2d(sb, &tb_hi, fb, kb * kTcBlockK, 0);
                     tma_load_2d(sb + b_bytes, &tb_lo, fb, kb * kTcBlockK, 0);
-                    issued_phase[stage] = phase;
-                    issued_mask |= 1 << stage;
+                    issued_phase[rs.stage] = rs.phase;
+                    issued_mask |= 1 << rs.stage;
                 }
-                const int k0 = kb * (kTcBlockK / 2);  // 32 samples per K block
-                uint32_t hi[32], lo[32];
-                // vector path: rows of axT and y start 16-byte aligned only when nk is even
-                if (iv && k0 + 32 <= P.nk && (P.nk & 1) == 0) {
+                // staged A_x^H half-row (128-byte swizzled) and y_c chunk
+                const uint8_t *arow = raw + (size_t)rr.stage * kRawBytes + h * (kRawBytes / 2) + ii * 128;
+                const float4 *yv4 = reinterpret_cast<const float4 *>(yraw + (size_t)rr.stage * kRawYBytes + h * 128);
+                float2 uval[16];
 #pragma unroll
-                    for (int q = 0; q < 32; q += 2) {
-                        const float4 av = __ldg(reinterpret_cast<const float4 *>(arow + k0 + q));
-                        const float4 yv = __ldg(reinterpret_cast<const float4 *>(yc + k0 + q));
-                        const float2 u0 = cmulc(make_float2(av.x, av.y), make_float2(yv.x, yv.y));
-                        const float2 u1 = cmulc(make_float2(av.z, av.w), make_float2(yv.z, yv.w));
-                        if (o == 0) {
-                            split2(u0.x, -u0.y, hi[q], lo[q]);
-                            split2(u1.x, -u1.y, hi[q + 1], lo[q + 1]);
-                        } else {
-                            split2(u0.y, u0.x, hi[q], lo[q]);
-                            split2(u1.y, u1.x, hi[q + 1], lo[q + 1]);
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        const int kappa = k0 + q;
-                        float2 uv = make_float2(0.f, 0.f);
-                        if (iv && kappa < P.nk) uv = cmulc(arow[kappa], yc[kappa]);
-                        if (o == 0)
-                            split2(uv.x, -uv.y, hi[q], lo[q]);
-                        else
-                            split2(uv.y, uv.x, hi[q], lo[q]);
-                    }
+                for (int c8 = 0; c8 < 8; ++c8) {
+                    const float4 av = *reinterpret_cast<const float4 *>(arow + ((c8 ^ (ii & 7)) << 4));
+                    const float4 yv = yv4[c8];
+                    uval[2 * c8] = cmulc(make_float2(av.x, av.y), make_float2(yv.x, yv.y));
+                    uval[2 * c8 + 1] = cmulc(make_float2(av.z, av.w), make_float2(yv.z, yv.w));
                 }
-                const int row = 2 * ii + o;
+                mbar_arrive(rempty0 + 8 * rr.stage);
+                rr.next(R);
+                // threads with h = 0 store their Re row first and threads with
+                // h = 1 their Im row, so that each store of the warp spreads
+                // over all eight 16-byte bank groups of the swizzled tile
+                const int row_first = 2 * ii + h, row_second = 2 * ii + (h ^ 1);
 #pragma unroll
-                for (int ch = 0; ch < 8; ++ch) {
-                    const uint32_t off = sw128_offset(row, ch * 16);
-                    *reinterpret_cast<uint4 *>(sbase + off) =
-                        make_uint4(hi[4 * ch], hi[4 * ch + 1], hi[4 * ch + 2], hi[4 * ch + 3]);
-                    *reinterpret_cast<uint4 *>(sbase + kTileBytesA + off) =
-                        make_uint4(lo[4 * ch], lo[4 * ch + 1], lo[4 * ch + 2], lo[4 * ch + 3]);
+                for (int cc = 0; cc < 4; ++cc) {
+                    uint32_t hr[4], lr[4], hm[4], lm[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) split_embed(uval[4 * cc + e], hr[e], lr[e], hm[e], lm[e]);
+                    const int colb = 64 * h + 16 * cc;
+                    const uint32_t o1 = sw128_offset(row_first, colb), o2 = sw128_offset(row_second, colb);
+                    const uint4 re_hi = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+                    const uint4 re_lo = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+                    const uint4 im_hi = make_uint4(hm[0], hm[1], hm[2], hm[3]);
+                    const uint4 im_lo = make_uint4(lm[0], lm[1], lm[2], lm[3]);
+                    *reinterpret_cast<uint4 *>(sbase + o1) = h ? im_hi : re_hi;
+                    *reinterpret_cast<uint4 *>(sbase + kTileBytesA + o1) = h ? im_lo : re_lo;
+                    *reinterpret_cast<uint4 *>(sbase + o2) = h ? re_hi : im_hi;
+                    *reinterpret_cast<uint4 *>(sbase + kTileBytesA + o2) = h ? re_lo : im_lo;
                 }
                 fence_proxy_async_smem();
                 mbar_arrive(fb);
-                if (++stage == S) {
-                    stage = 0;
-                    phase ^= 1;
-                }
+                rs.next(S);
             }
             if (!ok) break;
         }
@@ -453,10 +506,10 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
             for (int s = 0; s < S; ++s)
                 if (issued_mask & (1 << s)) drain_wait(full0 + 8 * s, issued_phase[s]);
     } else if (warp == 4) {
+        // UMMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32(kTcBlockM, P.ny_pad);
-            int stage = 0;
-            uint32_t phase = 0;
+            Ring rg;
             int lt = 0;
             bool issued_any = false;
             for (int u = blockIdx.x; u < P.num_units; u += gridDim.x, ++lt) {
@@ -469,12 +522,12 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                 const uint32_t d_tmem = tmem_base + (uint32_t)(a * P.ny_pad);
                 bool ok = true;
                 for (int kb = kb0; kb < kb1; ++kb) {
-                    if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, kWaitLimitNs)) {
+                    if (!mbar_wait(full0 + 8 * rg.stage, rg.phase, abort_flag, kWaitLimitNs)) {
                         ok = false;
                         break;
                     }
                     fence_after_sync();
-                    const uint32_t sa_hi = smem_u32(smem + (size_t)stage * stage_bytes);
+                    const uint32_t sa_hi = smem_u32(smem + (size_t)rg.stage * stage_bytes);
                     const uint32_t sa_lo = sa_hi + kTileBytesA;
                     const uint32_t sb_hi = sa_hi + 2 * kTileBytesA;
                     const uint32_t sb_lo = sb_hi + b_bytes;
@@ -488,11 +541,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                         umma_f16(d_tmem, dal, dbh, idesc, 1u);
                     }
                     issued_any = true;
-                    umma_commit(empty0 + 8 * stage);
-                    if (++stage == S) {
-                        stage = 0;
-                        phase ^= 1;
-                    }
+                    umma_commit(empty0 + 8 * rg.stage);
+                    rg.next(S);
                 }
                 if (!ok) break;
                 umma_commit(tfull0 + 8 * a);
@@ -501,6 +551,33 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                 umma_commit(fin);
                 drain_wait(fin, 0);
             }
+        }
+    } else if (warp == 9) {
+        // loader of the A_x^H tiles (two 128-byte-swizzled halves) and the y_c chunks
+        if (lane == 0) {
+            Ring rg;
+            uint32_t issued_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            int issued_mask = 0;
+            for (int u = blockIdx.x; u < P.num_units && !*abort_flag; u += gridDim.x) {
+                const int p = u / P.m_tiles, m = u % P.m_tiles;
+                const int c = m / P.tiles_per_coil, ib = m % P.tiles_per_coil;
+                const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    if (!mbar_wait(rempty0 + 8 * rg.stage, rg.phase ^ 1, abort_flag, kWaitLimitNs)) break;
+                    const uint32_t rb = rfull0 + 8 * rg.stage;
+                    const uint32_t dst = smem_u32(raw + (size_t)rg.stage * kRawBytes);
+                    mbar_arrive_expect_tx(rb, kRawBytes + kRawYBytes);
+                    tma_load_2d(dst, &t_axT, rb, kb * 64, ib * 64);
+                    tma_load_2d(dst + kRawBytes / 2, &t_axT, rb, kb * 64 + 32, ib * 64);
+                    tma_load_2d(smem_u32(yraw + (size_t)rg.stage * kRawYBytes), &t_y, rb, kb * 64, c);
+                    issued_phase[rg.stage] = rg.phase;
+                    issued_mask |= 1 << rg.stage;
+                    rg.next(R);
+                }
+            }
+            if (*abort_flag)
+                for (int r = 0; r < R; ++r)
+                    if (issued_mask & (1 << r)) drain_wait(rfull0 + 8 * r, issued_phase[r]);
         }
     } else {
         // epilogue: warps 5..8; TMEM lane quadrant = warp % 4
@@ -567,22 +644,22 @@ EncodeTiledFn get_encode_fn() {
     return fn;
 }
 
-// 2-D bf16 tensor [rows][cols] (cols contiguous), box = 64 cols x box_rows, 128-byte swizzle.
-bool make_map(CUtensorMap *m, void *base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+// 2-D tensor [rows][cols] (cols contiguous) of `elem`-byte elements, box = box_cols x box_rows.
+bool make_map(CUtensorMap *m, CUtensorMapDataType type, int elem, void *base, uint64_t cols, uint64_t rows,
+              uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle swz) {
     EncodeTiledFn fn = get_encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {cols, rows};
-    cuuint64_t strides[1] = {cols * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kTcBlockK, box_rows};
+    cuuint64_t strides[1] = {cols * (uint64_t)elem};
+    cuuint32_t box[2] = {box_cols, box_rows};
     cuuint32_t estr[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return fn(m, type, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int stages_for(uint32_t stage_bytes) {
-    const int avail = kMaxSmem - 1024 - 256;
-    return std::min(4, avail / (int)stage_bytes);
+bool make_bf16_map(CUtensorMap *m, void *base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+    return make_map(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, cols, rows, kTcBlockK, box_rows,
+                    CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
 uint32_t tmem_cols_for(int cols) {
@@ -591,14 +668,28 @@ uint32_t tmem_cols_for(int cols) {
     return n;
 }
 
-size_t fwd_smem_bytes(const mri_plan *p) {
-    const uint32_t stage = 2u * kTileBytesA + 2u * (uint32_t)p->fwd_block_n * 128u;
-    return 1024 + (size_t)stages_for(stage) * stage + 256;
+// shared-memory plans: (operand stages, secondary ring stages, bytes)
+void fwd_smem_plan(const mri_plan *p, int *stages, int *ay_stages, size_t *bytes) {
+    const int stage = 2 * kTileBytesA + 2 * p->fwd_block_n * 128;
+    int r = 2;
+    int s = std::min(4, (kMaxSmem - kSmemSlack - r * kAyChunkBytes) / stage);
+    if (s >= 3 && kMaxSmem - kSmemSlack - s * stage >= 3 * kAyChunkBytes) r = 3;
+    *stages = s;
+    *ay_stages = r;
+    *bytes = (size_t)kSmemSlack + (size_t)s * stage + (size_t)r * kAyChunkBytes;
 }
 
-size_t adj_smem_bytes(const mri_plan *p) {
-    const uint32_t stage = 2u * kTileBytesA + 2u * (uint32_t)p->ny_pad * 128u;
-    return 1024 + (size_t)stages_for(stage) * stage + 256;
+void adj_smem_plan(const mri_plan *p, int *stages, int *raw_stages, size_t *bytes) {
+    const int stage = 2 * kTileBytesA + 2 * p->ny_pad * 128;
+    const int raw = kRawBytes + kRawYBytes;
+    // the staged A_x^H / y tiles come from L2 or HBM: prefer a deep raw ring
+    // (up to 6) over a third operand stage
+    int s = 2;
+    if (kMaxSmem - kSmemSlack - 3 * stage >= 4 * raw) s = 3;
+    int r = std::min(6, (kMaxSmem - kSmemSlack - s * stage) / raw);
+    *stages = s;
+    *raw_stages = r;
+    *bytes = (size_t)kSmemSlack + (size_t)s * stage + (size_t)r * raw;
 }
 
 }  // namespace
@@ -624,7 +715,7 @@ bool tc_supported(const mri_plan *p, std::string *why) {
 
 int tc_plan_tiling(mri_plan *p) {
     // forward: whole coils per N tile
-    const int cpt_max = std::max(1, 256 / p->ny_pad);
+    const int cpt_max = std::min(kMaxCoilsPerTile, std::max(1, 256 / p->ny_pad));
     const int n_tiles = ceil_div(p->nc, cpt_max);
     p->fwd_coils_per_tile = ceil_div(p->nc, n_tiles);
     p->fwd_block_n = p->fwd_coils_per_tile * p->ny_pad;
@@ -649,17 +740,29 @@ int tc_plan_tiling(mri_plan *p) {
     }
     p->ksplit_blocks = ceil_div(num_kb, best_split);
     p->ksplit = ceil_div(num_kb, p->ksplit_blocks);
-    if (fwd_smem_bytes(p) > (size_t)kMaxSmem || adj_smem_bytes(p) > (size_t)kMaxSmem) return MRI_ERR_UNSUPPORTED;
+    int s, r;
+    size_t fb, ab;
+    fwd_smem_plan(p, &s, &r, &fb);
+    if (s < 2) return MRI_ERR_UNSUPPORTED;
+    adj_smem_plan(p, &s, &r, &ab);
+    if (s < 2 || r < 2) return MRI_ERR_UNSUPPORTED;
     return MRI_OK;
 }
 
 int tc_make_tensor_maps(mri_plan *p) {
-    bool ok = make_map(&p->tm_afwd_hi, p->afwd_hi, p->kx, 2ull * p->nk, kTcBlockM) &&
-              make_map(&p->tm_afwd_lo, p->afwd_lo, p->kx, 2ull * p->nk, kTcBlockM) &&
-              make_map(&p->tm_bfwd_hi, p->bfwd_hi, p->kx, (uint64_t)p->nc * p->ny_pad, p->fwd_block_n) &&
-              make_map(&p->tm_bfwd_lo, p->bfwd_lo, p->kx, (uint64_t)p->nc * p->ny_pad, p->fwd_block_n) &&
-              make_map(&p->tm_badj_hi, p->badj_hi, p->kk, p->ny_pad, p->ny_pad) &&
-              make_map(&p->tm_badj_lo, p->badj_lo, p->kk, p->ny_pad, p->ny_pad);
+    const uint64_t nkf = 2ull * p->nk_pad;  // floats per sample-indexed row
+    bool ok = make_bf16_map(&p->tm_afwd_hi, p->afwd_hi, p->kx, 2ull * p->nk, kTcBlockM) &&
+              make_bf16_map(&p->tm_afwd_lo, p->afwd_lo, p->kx, 2ull * p->nk, kTcBlockM) &&
+              make_bf16_map(&p->tm_bfwd_hi, p->bfwd_hi, p->kx, (uint64_t)p->nc * p->ny_pad, p->fwd_block_n) &&
+              make_bf16_map(&p->tm_bfwd_lo, p->bfwd_lo, p->kx, (uint64_t)p->nc * p->ny_pad, p->fwd_block_n) &&
+              make_bf16_map(&p->tm_badj_hi, p->badj_hi, p->kk, p->ny_pad, p->ny_pad) &&
+              make_bf16_map(&p->tm_badj_lo, p->badj_lo, p->kk, p->ny_pad, p->ny_pad) &&
+              make_map(&p->tm_axT, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->axT, nkf, p->nx, 32, 64,
+                       CU_TENSOR_MAP_SWIZZLE_128B) &&
+              make_map(&p->tm_y, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->y, nkf, p->nc, 64, 1,
+                       CU_TENSOR_MAP_SWIZZLE_NONE) &&
+              make_map(&p->tm_ayT, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->ayT, nkf, p->ny, 128, 32,
+                       CU_TENSOR_MAP_SWIZZLE_NONE);
     if (!ok) {
         set_error("cuTensorMapEncodeTiled failed");
         return MRI_ERR_CUDA;
@@ -674,16 +777,15 @@ int tc_make_tensor_maps(mri_plan *p) {
     return MRI_OK;
 }
 
-cudaError_t launch_fwd_tc(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace, int skip,
+cudaError_t launch_fwd_tc(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace, int ld, int skip,
                           cudaStream_t s) {
-    dim3 og(ceil_div(p->nx, 32), ceil_div(p->ny, 32));
+    dim3 og(ceil_div(p->nx, 32), ceil_div(p->ny, 32), p->nc);
     fwd_operand_kernel<<<og, dim3(32, 8), 0, s>>>(image, maps, (uint32_t *)p->bfwd_hi, (uint32_t *)p->bfwd_lo, p->nx,
-                                                  p->ny, p->ny_pad, p->kx, p->nc, p->scal, skip);
+                                                  p->ny, p->ny_pad, p->kx, p->scal, skip);
     FwdParams P;
-    P.ayT = p->ayT;
     P.y = kspace;
+    P.y_ld = ld;
     P.nk = p->nk;
-    P.ny = p->ny;
     P.ny_pad = p->ny_pad;
     P.nc = p->nc;
     P.cpt = p->fwd_coils_per_tile;
@@ -691,28 +793,25 @@ cudaError_t launch_fwd_tc(mri_plan *p, const float2 *image, const float2 *maps, 
     P.n_tiles = p->fwd_n_tiles;
     P.num_tiles = p->fwd_m_tiles * p->fwd_n_tiles;
     P.num_kb = p->kx / kTcBlockK;
-    const uint32_t stage = 2u * kTileBytesA + 2u * (uint32_t)p->fwd_block_n * 128u;
-    P.stages = stages_for(stage);
+    size_t smem;
+    fwd_smem_plan(p, &P.stages, &P.ay_stages, &smem);
     P.tmem_cols = tmem_cols_for(2 * p->fwd_block_n);
     P.sc = p->scal;
     P.skip = skip;
     P.status = &p->scal->status;
     const int grid = std::min(P.num_tiles, p->num_sms);
     timing_begin(p, s);
-    fwd_tc_kernel<<<grid, kFwdThreads, fwd_smem_bytes(p), s>>>(p->tm_afwd_hi, p->tm_afwd_lo, p->tm_bfwd_hi,
-                                                               p->tm_bfwd_lo, P);
+    fwd_tc_kernel<<<grid, kFwdThreads, smem, s>>>(p->tm_afwd_hi, p->tm_afwd_lo, p->tm_bfwd_hi, p->tm_bfwd_lo,
+                                                  p->tm_ayT, P);
     timing_end(p, s);
     p->launches += 2;
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_tc(mri_plan *p, const float2 *kspace, int skip, cudaStream_t s) {
+cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
     AdjParams P;
-    P.axT = p->axT;
-    P.y = kspace;
     P.part = p->part;
     P.nx = p->nx;
-    P.nk = p->nk;
     P.ny = p->ny;
     P.ny_pad = p->ny_pad;
     P.nx_pad = p->nx_pad;
@@ -722,15 +821,15 @@ cudaError_t launch_adj_tc(mri_plan *p, const float2 *kspace, int skip, cudaStrea
     P.kb_per_split = p->ksplit_blocks;
     P.num_kb = p->kk / kTcBlockK;
     P.num_units = p->adj_m_tiles * p->ksplit;
-    const uint32_t stage = 2u * kTileBytesA + 2u * (uint32_t)p->ny_pad * 128u;
-    P.stages = stages_for(stage);
+    size_t smem;
+    adj_smem_plan(p, &P.stages, &P.raw_stages, &smem);
     P.tmem_cols = tmem_cols_for(2 * p->ny_pad);
     P.sc = p->scal;
     P.skip = skip;
     P.status = &p->scal->status;
     const int grid = std::min(P.num_units, p->num_sms);
     timing_begin(p, s);
-    adj_tc_kernel<<<grid, kAdjThreads, adj_smem_bytes(p), s>>>(p->tm_badj_hi, p->tm_badj_lo, P);
+    adj_tc_kernel<<<grid, kAdjThreads, smem, s>>>(p->tm_badj_hi, p->tm_badj_lo, p->tm_axT, p->tm_y, P);
     timing_end(p, s);
     p->launches += 1;
     return cudaGetLastError();

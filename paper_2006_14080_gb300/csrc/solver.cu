@@ -42,63 +42,58 @@ __device__ __forceinline__ float2 theta_h_theta_at(const float2 *p, int i, int j
 }
 
 // out[i][j] = sum_c conj(S_c[i][j]) sum_p part[p][c][j][i]  (+ half_beta Theta^H Theta tv_src)
-// and optionally Re<dot_src, out> -> alpha = tau / dot.  Block (32, 8) covers
-// a 32 x 32 tile; the partials are read coalesced along i and transposed
-// through shared memory.
-__global__ void __launch_bounds__(256) adj_reduce_kernel(const float2 *__restrict__ part, int ksplit, int nc,
-                                                         int nx, int ny, int nx_pad, const float2 *__restrict__ maps,
-                                                         float2 *__restrict__ out, const float2 *__restrict__ tv_src,
-                                                         float half_beta, const float2 *__restrict__ dot_src,
-                                                         DevScalars *sc, double *partials, int skip) {
+// and optionally Re<dot_src, out> -> alpha = tau / dot.  Block (32, 16)
+// covers 32 consecutive pixels i of one column j; thread row ty takes the
+// (split, coil) pairs q = ty, ty + 16, ... (reads coalesced along i, four in
+// flight), and the sixteen groups are then added in a fixed order.
+constexpr int kReduceGroups = 16;
+__global__ void __launch_bounds__(32 * kReduceGroups)
+    adj_reduce_kernel(const float2 *__restrict__ part, int ksplit, int nc, int nx, int ny, int nx_pad,
+                      const float2 *__restrict__ maps, float2 *__restrict__ out, const float2 *__restrict__ tv_src,
+                      float half_beta, const float2 *__restrict__ dot_src, DevScalars *sc, double *partials,
+                      int skip) {
     if (should_skip(sc, skip)) return;
-    __shared__ float2 tile[32][33];
+    __shared__ float2 grp[kReduceGroups][32];
     __shared__ double red[32];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const int i = blockIdx.x * 32 + tx, j = blockIdx.y;
     const size_t npix = (size_t)nx * ny;
-    float2 acc[4];
+    const int npairs = ksplit * nc;  // pair q = p * nc + c, stored at part + q * ny * nx_pad
+    float2 acc = make_float2(0.f, 0.f);
+    if (i < nx) {
+        const float2 *src = part + (size_t)j * nx_pad + i;
+        const float2 *S = maps + (size_t)i * ny + j;
+        const size_t pstride = (size_t)ny * nx_pad;
+        int q = ty;
+        for (; q + 3 * kReduceGroups < npairs; q += 4 * kReduceGroups) {
+            float2 w[4], s[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
-    for (int c = 0; c < nc; ++c) {
-        float2 w[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) w[q] = make_float2(0.f, 0.f);
-        const int ii = i0 + tx;
-        for (int p = 0; p < ksplit; ++p) {
-            const float2 *src = part + ((size_t)p * nc + c) * ny * nx_pad;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int jj = j0 + ty + 8 * q;
-                if (ii < nx && jj < ny) w[q] = cadd(w[q], src[(size_t)jj * nx_pad + ii]);
+            for (int e = 0; e < 4; ++e) {
+                const int qq = q + e * kReduceGroups;
+                w[e] = src[(size_t)qq * pstride];
+                s[e] = S[(size_t)(qq % nc) * npix];
             }
-        }
-        __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 4; ++q) tile[ty + 8 * q][tx] = w[q];
-        __syncthreads();
-        const float2 *S = maps + (size_t)c * npix;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = i0 + ty + 8 * q, j = j0 + tx;
-            if (i < nx && j < ny) acc[q] = cadd(acc[q], cmulc(S[(size_t)i * ny + j], tile[tx][ty + 8 * q]));
+            for (int e = 0; e < 4; ++e) acc = cadd(acc, cmulc(s[e], w[e]));
         }
+        for (; q < npairs; q += kReduceGroups) acc = cadd(acc, cmulc(S[(size_t)(q % nc) * npix], src[(size_t)q * pstride]));
     }
+    grp[ty][tx] = acc;
+    __syncthreads();
     double dot = 0.0;
+    if (ty == 0 && i < nx) {
+        float2 v = grp[0][tx];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int i = i0 + ty + 8 * q, j = j0 + tx;
-        if (i < nx && j < ny) {
-            float2 v = acc[q];
-            if (tv_src) {
-                const float2 t = theta_h_theta_at(tv_src, i, j, nx, ny);
-                v.x = fmaf(half_beta, t.x, v.x);
-                v.y = fmaf(half_beta, t.y, v.y);
-            }
-            out[(size_t)i * ny + j] = v;
-            if (dot_src) {
-                const float2 dv = dot_src[(size_t)i * ny + j];
-                dot += (double)dv.x * (double)v.x + (double)dv.y * (double)v.y;
-            }
+        for (int g = 1; g < kReduceGroups; ++g) v = cadd(v, grp[g][tx]);
+        if (tv_src) {
+            const float2 t = theta_h_theta_at(tv_src, i, j, nx, ny);
+            v.x = fmaf(half_beta, t.x, v.x);
+            v.y = fmaf(half_beta, t.y, v.y);
+        }
+        out[(size_t)i * ny + j] = v;
+        if (dot_src) {
+            const float2 dv = dot_src[(size_t)i * ny + j];
+            dot = (double)dv.x * (double)v.x + (double)dv.y * (double)v.y;
         }
     }
     if (dot_src) {
@@ -268,7 +263,7 @@ __global__ void admm_dual_kernel(int nx, int ny, const float2 *__restrict__ x, c
 
 // f = ||y - d||^2 + lambda sum |Theta x|  (Eq. 3), with y = F x already in
 // yfx.  Recorded for every step that ran, including the one that met rtol.
-__global__ void objective_kernel(int nx, int ny, int nkc, const float2 *__restrict__ yfx,
+__global__ void objective_kernel(int nx, int ny, int nk, int nkc, const float2 *__restrict__ yfx, int yfx_ld,
                                  const float2 *__restrict__ kspace, const float2 *__restrict__ x, float lambda,
                                  DevScalars *sc, double *partials, double *obj_hist, int m) {
     if (!sc->step_active) return;
@@ -276,7 +271,7 @@ __global__ void objective_kernel(int nx, int ny, int nkc, const float2 *__restri
     const int npix = nx * ny;
     double fid = 0.0, l1 = 0.0;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < nkc; n += gridDim.x * blockDim.x) {
-        const float2 r = csub(yfx[n], kspace[n]);
+        const float2 r = csub(yfx[(size_t)(n / nk) * yfx_ld + n % nk], kspace[n]);
         fid += (double)r.x * r.x + (double)r.y * r.y;
     }
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < npix; n += gridDim.x * blockDim.x) {
@@ -309,8 +304,8 @@ int ew_blocks(int n) { return max(1, min(kEwMaxBlocks, ceil_div(n, kEwThreads)))
 
 cudaError_t launch_adj_reduce(mri_plan *p, const float2 *maps, float2 *out, const ReduceEpilogue &e,
                               cudaStream_t s) {
-    dim3 grid(ceil_div(p->nx, 32), ceil_div(p->ny, 32));
-    adj_reduce_kernel<<<grid, dim3(32, 8), 0, s>>>(p->part, p->ksplit, p->nc, p->nx, p->ny, p->nx_pad, maps, out,
+    dim3 grid(ceil_div(p->nx, 32), p->ny);
+    adj_reduce_kernel<<<grid, dim3(32, kReduceGroups), 0, s>>>(p->part, p->ksplit, p->nc, p->nx, p->ny, p->nx_pad, maps, out,
                                                    e.tv_src, e.half_beta, e.dot_src, p->scal, p->partials, e.skip);
     return cudaGetLastError();
 }
@@ -371,8 +366,9 @@ cudaError_t launch_objective(mri_plan *p, const float2 *kspace, float lambda, do
                              cudaStream_t s) {
     const int npix = p->nx * p->ny;
     const int nkc = p->nk * p->nc;
-    objective_kernel<<<ew_blocks(max(npix, nkc)), kEwThreads, 0, s>>>(p->nx, p->ny, nkc, p->y, kspace, p->x, lambda,
-                                                                      p->scal, p->partials, obj_hist, m);
+    objective_kernel<<<ew_blocks(max(npix, nkc)), kEwThreads, 0, s>>>(p->nx, p->ny, p->nk, nkc, p->y, p->nk_pad,
+                                                                      kspace, p->x, lambda, p->scal, p->partials,
+                                                                      obj_hist, m);
     return cudaGetLastError();
 }
 
