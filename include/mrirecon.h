@@ -174,6 +174,29 @@ MRI_API int mri_admm_reconstruct(mri_plan *plan, const mri_c64 *kspace, const mr
                                  double *objective_hist, double *alpha_hist, mri_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Allocation-free adjoint (the paper has no counterpart; it is a convenience
+ * for callers that cannot allocate device memory -- code running where the
+ * CUDA allocator must not be touched, such as a real-time loop, a host
+ * callback, or a process whose device memory is reserved up front).
+ *
+ * Same result as mri_nudft_adjoint with an MRI_FP32 plan, but needs no plan
+ * and allocates nothing: the DFT factors are formed on the fly from traj
+ * (device, [nk][2] float) and the k-space-split partial images live in a
+ * fixed 16 MiB device buffer that the library holds on every GPU that loads
+ * it, until the process exits.  kspace [nc][nk], coil_maps [nc][nx][ny] and
+ * image [nx][ny] are device arrays owned by the caller.
+ *   - nc * nx * ny must not exceed 2097152 (16 MiB of complex64), else
+ *     MRI_ERR_INVALID with a message naming the limit.
+ *   - all calls on a device share the buffer and it keeps the last call's
+ *     contents; calls that overlap on the GPU (unordered streams) race on
+ *     it, so serialise them.
+ *   - the first call on a device looks up the buffer's address; make it
+ *     before any stream capture.
+ * ------------------------------------------------------------------------- */
+MRI_API int mri_nudft_adjoint_noalloc(int nx, int ny, int nk, int nc, const float *traj, const mri_c64 *kspace,
+                                      const mri_c64 *coil_maps, mri_c64 *image, mri_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Diagnostics (not in the paper): kernel accounting used by benchmarks.
  * ------------------------------------------------------------------------- */
 

@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH):
         "mri_tv_adjoint": ([I, I, P, P, P], I),
         "mri_soft_threshold": ([I, F, P, P, P], I),
         "mri_admm_reconstruct": ([P, P, P, ctypes.POINTER(AdmmParams), P, P, P, P], I),
+        "mri_nudft_adjoint_noalloc": ([I, I, I, I, P, P, P, P, P], I),
         "mri_plan_set_timing": ([P, I], I),
         "mri_plan_read_timing": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
                                   ctypes.POINTER(ctypes.c_longlong)], I),
@@ -197,6 +198,21 @@ def nudft_adjoint(plan: Plan, kspace, coil_maps, out=None, stream=None):
         out = torch.empty((plan.nx, plan.ny), dtype=torch.complex64, device=kspace.device)
     _need(out, torch.complex64, (plan.nx, plan.ny), "image")
     _check(load().mri_nudft_adjoint(plan.handle, _ptr(kspace), _ptr(coil_maps), _ptr(out), _stream(stream)))
+    return out
+
+
+def nudft_adjoint_noalloc(traj, kspace, coil_maps, out, stream=None):
+    """Adjoint DFT without a plan and without any device allocation by the
+    library (``mri_nudft_adjoint_noalloc``): for callers that must not touch
+    the CUDA allocator.  ``out`` is required (the caller owns all memory)."""
+    nc, nx, ny = coil_maps.shape
+    nk = traj.shape[0]
+    _need(traj, torch.float32, (nk, 2), "traj")
+    _need(kspace, torch.complex64, (nc, nk), "kspace")
+    _need(coil_maps, torch.complex64, (nc, nx, ny), "coil_maps")
+    _need(out, torch.complex64, (nx, ny), "image")
+    _check(load().mri_nudft_adjoint_noalloc(nx, ny, nk, nc, _ptr(traj), _ptr(kspace), _ptr(coil_maps), _ptr(out),
+                                            _stream(stream)))
     return out
 
 
