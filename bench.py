@@ -185,6 +185,7 @@ def run_gpu(args, rank, world, local_rank):
     results = {}
     out = torch.empty((p.nx, p.ny), dtype=torch.complex64, device=dev)
     with mr.Plan(p.nx, p.ny, p.nc, traj, "bf16x3") as plan:
+        tuned = plan.autotune(repeats=5)  # set-up, outside the timed region
         gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]) \
             if os.environ.get("CUDA_VISIBLE_DEVICES") else local_rank
         with ClockSampler(gpu_index) as clk:
@@ -262,6 +263,7 @@ def run_gpu(args, rank, world, local_rank):
         "e2e": {"value": world * args.steps / (e2e_ms / 1e3), "unit": "recon/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "tuning": tuned,
         "roofline": {"bound": "tensor", "kernel": "adj_tc_kernel" if dom == "adj" else "fwd_tc_kernel",
                      "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf,
                      "traffic": None,

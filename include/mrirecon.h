@@ -214,6 +214,27 @@ MRI_API int mri_plan_read_timing(mri_plan *plan, double *fwd_ms, long long *fwd_
 /* Number of kernels this plan has enqueued since creation. */
 MRI_API long long mri_plan_launch_count(const mri_plan *plan);
 
+/* ---------------------------------------------------------------------------
+ * Scheduling of the tensor-core products (not in the paper).  The forward
+ * and adjoint kernels run as clusters of 1, 2, 4 or 8 CTAs that share (TMA
+ * multicast) the operand common to their tiles.  The cluster size changes
+ * the schedule only, never the arithmetic or its order.
+ * ------------------------------------------------------------------------- */
+
+/* Current configuration (nullable outputs): cluster sizes, number of
+ * k-space splits of the adjoint, coils per forward tile. */
+MRI_API int mri_plan_get_config(const mri_plan *plan, int *fwd_cluster, int *adj_cluster, int *adj_ksplit,
+                                int *fwd_coils_per_tile);
+
+/* Set the cluster sizes (0 keeps the current one); MRI_ERR_INVALID when a
+ * size does not divide the tile shape; MRI_ERR_UNSUPPORTED on an FP32 plan. */
+MRI_API int mri_plan_set_clusters(mri_plan *plan, int fwd_cluster, int adj_cluster);
+
+/* Autotuner: time every valid cluster size of both products on this plan's
+ * shape (`repeats` launches each, default 3) and keep the fastest.
+ * Synchronises `stream`; allocates a temporary buffer.  No-op for FP32 plans. */
+MRI_API int mri_plan_autotune(mri_plan *plan, int repeats, mri_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,9 @@ def load(path: str = LIB_PATH):
         "mri_plan_read_timing": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
                                   ctypes.POINTER(ctypes.c_longlong)], I),
         "mri_plan_launch_count": ([P], ctypes.c_longlong),
+        "mri_plan_get_config": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "mri_plan_set_clusters": ([P, I, I], I),
+        "mri_plan_autotune": ([P, I, P], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -162,6 +165,20 @@ class Plan:
 
     def launch_count(self) -> int:
         return int(load().mri_plan_launch_count(self.handle))
+
+    def config(self) -> dict:
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(load().mri_plan_get_config(self.handle, *[ctypes.byref(q) for q in v]))
+        return {"fwd_cluster": v[0].value, "adj_cluster": v[1].value, "adj_ksplit": v[2].value,
+                "fwd_coils_per_tile": v[3].value}
+
+    def set_clusters(self, fwd: int = 0, adj: int = 0):
+        _check(load().mri_plan_set_clusters(self.handle, int(fwd), int(adj)))
+
+    def autotune(self, repeats: int = 3, stream=None) -> dict:
+        """Time the valid cluster sizes of both products on this shape and keep the fastest."""
+        _check(load().mri_plan_autotune(self.handle, int(repeats), _stream(stream)))
+        return self.config()
 
     def close(self):
         if getattr(self, "_h", None) is not None:

@@ -440,4 +440,84 @@ MRI_API int mri_plan_read_timing(mri_plan *p, double *fwd_ms, long long *fwd_lau
 
 MRI_API long long mri_plan_launch_count(const mri_plan *p) { return p ? p->launches : 0; }
 
+MRI_API int mri_plan_get_config(const mri_plan *p, int *fwd_cluster, int *adj_cluster, int *adj_ksplit,
+                                int *fwd_coils_per_tile) {
+    if (!p) return fail(MRI_ERR_INVALID, "null plan");
+    if (fwd_cluster) *fwd_cluster = p->fwd_cluster;
+    if (adj_cluster) *adj_cluster = p->adj_cluster;
+    if (adj_ksplit) *adj_ksplit = p->ksplit;
+    if (fwd_coils_per_tile) *fwd_coils_per_tile = p->fwd_coils_per_tile;
+    return MRI_OK;
+}
+
+MRI_API int mri_plan_set_clusters(mri_plan *p, int fwd_cluster, int adj_cluster) {
+    if (!p) return fail(MRI_ERR_INVALID, "null plan");
+    if (p->precision != MRI_BF16X3) return fail(MRI_ERR_UNSUPPORTED, "cluster sizes apply to the tensor-core form");
+    return tc_set_clusters(p, fwd_cluster, adj_cluster);
+}
+
+// Times every valid cluster size of the two product kernels on this plan's
+// shape (the data do not change the work, so the plan's zeroed workspace is
+// used) and keeps the fastest.  The choice changes scheduling only, never the
+// arithmetic or its order.  Allocates a temporary coil-map buffer and
+// synchronises the stream.
+MRI_API int mri_plan_autotune(mri_plan *p, int repeats, mri_stream_t stream) {
+    if (!p) return fail(MRI_ERR_INVALID, "null plan");
+    if (p->precision != MRI_BF16X3) return MRI_OK;  // the FP32 form has nothing to tune
+    if (repeats <= 0) repeats = 3;
+    cudaStream_t s = (cudaStream_t)stream;
+    float2 *maps = nullptr;
+    const size_t npix = (size_t)p->nx * p->ny;
+    if (cudaMalloc(&maps, (size_t)p->nc * npix * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MRI_ERR_NOMEM, "autotune: temporary coil maps");
+    }
+    cudaMemsetAsync(maps, 0, (size_t)p->nc * npix * sizeof(float2), s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool was_timing = p->timing;
+    p->timing = false;
+    int best_f = p->fwd_cluster, best_a = p->adj_cluster;
+    float best_tf = 1e30f, best_ta = 1e30f;
+    int rc = MRI_OK;
+    const int cands[] = {1, 2, 4, 8};
+    for (int which = 0; which < 2 && rc == MRI_OK; ++which) {
+        for (int cm : cands) {
+            const bool valid = which == 0 ? tc_cluster_valid_fwd(p, cm) : tc_cluster_valid_adj(p, cm);
+            if (!valid) continue;
+            rc = which == 0 ? tc_set_clusters(p, cm, best_a) : tc_set_clusters(p, best_f, cm);
+            if (rc != MRI_OK) break;
+            cudaError_t e = cudaSuccess;
+            for (int it = 0; it <= repeats && e == cudaSuccess; ++it) {
+                if (it == 1) cudaEventRecord(e0, s);
+                e = which == 0 ? launch_fwd_tc(p, p->x, maps, p->y, p->nk_pad, kSkipNever, s)
+                               : launch_adj_tc(p, kSkipNever, s);
+            }
+            cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "autotune");
+                break;
+            }
+            if (which == 0 && ms < best_tf) {
+                best_tf = ms;
+                best_f = cm;
+            }
+            if (which == 1 && ms < best_ta) {
+                best_ta = ms;
+                best_a = cm;
+            }
+        }
+    }
+    if (rc == MRI_OK) rc = tc_set_clusters(p, best_f, best_a);
+    p->timing = was_timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(maps);
+    return rc;
+}
+
 }  // extern "C"

@@ -73,6 +73,8 @@ struct mri_plan {
     int nx_pad = 0;   // round_up(nx, 64): image rows per adjoint M tile group
     int fwd_coils_per_tile = 0, fwd_block_n = 0, fwd_n_tiles = 0, fwd_m_tiles = 0;
     int adj_m_tiles = 0, adj_block_n = 0;
+    int fwd_cluster = 1, adj_cluster = 1;    // CTAs per thread-block cluster (B operand multicast)
+    int fwd_grid = 0, adj_grid = 0;          // persistent grid sizes (co-resident CTAs)
     __nv_bfloat16 *afwd_hi = nullptr, *afwd_lo = nullptr;  // [2*nk][kx]
     __nv_bfloat16 *badj_hi = nullptr, *badj_lo = nullptr;  // [ny_pad][kk]
     __nv_bfloat16 *bfwd_hi = nullptr, *bfwd_lo = nullptr;  // [nc*ny_pad][kx]
@@ -129,6 +131,11 @@ cudaError_t launch_adj_fp32(mri_plan *p, int skip, cudaStream_t s);
 bool tc_supported(const mri_plan *p, std::string *why);
 int tc_plan_tiling(mri_plan *p);       // tile shapes and k-space splits; MRI_* status
 int tc_make_tensor_maps(mri_plan *p);  // TMA descriptors of the allocated operands; MRI_* status
+// Cluster sizes of the forward and adjoint products (1, 2, 4 or 8 where the
+// shape allows; 0 keeps the current one).  Rebuilds the tensor maps.
+int tc_set_clusters(mri_plan *p, int fwd_cm, int adj_cm);
+bool tc_cluster_valid_fwd(const mri_plan *p, int cm);
+bool tc_cluster_valid_adj(const mri_plan *p, int cm);
 cudaError_t launch_fwd_tc(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace, int ld,
                           int skip, cudaStream_t s);
 cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s);

@@ -49,14 +49,22 @@ constexpr int kAyChunkBytes = 32 * 64 * 8;        // 32 columns x 64 samples, co
 constexpr int kRawBytes = 2 * 64 * 128;           // 64 pixels x 32 samples of A_x^H, complex FP32
 constexpr int kRawYBytes = 32 * 8;                // 32 samples of y_c
 constexpr int kFwdThreads = 224;                  // w0 TMA, w1 UMMA, w2 A_y TMA, w3-6 epilogue
-constexpr int kAdjThreads = 320;                  // w0-3 producers, w4 UMMA, w5-8 epilogue, w9 TMA
+constexpr int kAdjProducerWarps = 8;              // adjoint: w0-7 producers, w8 UMMA, w9-12 epilogue, w13 TMA
+constexpr int kAdjProducers = 32 * kAdjProducerWarps;
+constexpr int kAdjMmaWarp = kAdjProducerWarps;
+constexpr int kAdjLoaderWarp = kAdjProducerWarps + 5;
+constexpr int kAdjThreads = 32 * (kAdjProducerWarps + 6);
 constexpr int kMaxSmem = 227 * 1024;
 constexpr int kSmemSlack = 1024 + 256;            // alignment + barriers
-constexpr int kMaxCoilsPerTile = 16;
+constexpr int kMaxCoilsPerTile = 4;
 
+// Work split of both kernels: clusters of `cm` CTAs process groups of cm
+// tiles (units) in lockstep; the operand shared by the group (B) is loaded
+// once, each CTA fetching 1/cm of its rows and multicasting them to all.
 struct FwdParams {
     float2 *y;  // [nc][y_ld]
-    int y_ld, nk, ny_pad, nc, cpt, block_n, n_tiles, num_tiles, num_kb, stages, ay_stages;
+    int y_ld, nk, ny_pad, nc, cpt, block_n, n_tiles, num_kb, stages, ay_stages;
+    int cm, num_groups;  // cluster size; groups = ceil(m_tiles / cm) * n_tiles
     uint32_t tmem_cols;
     const DevScalars *sc;
     int skip;
@@ -65,13 +73,16 @@ struct FwdParams {
 
 struct AdjParams {
     float2 *part;  // [ksplit][nc][ny][nx_pad]
-    int nx, ny, ny_pad, nx_pad, nc, tiles_per_coil, m_tiles, kb_per_split, num_kb, num_units;
+    int nx, ny, ny_pad, nx_pad, nc, tiles_per_coil, m_tiles, kb_per_split, num_kb;
     int stages, raw_stages;
+    int cm, num_groups;  // cluster size; groups = m_tiles * ksplit / cm
     uint32_t tmem_cols;
     const DevScalars *sc;
     int skip;
     int *status;
 };
+
+__device__ __forceinline__ uint16_t cluster_mask(int cm) { return (uint16_t)((1u << cm) - 1u); }
 
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
     return (uint8_t *)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
@@ -173,11 +184,15 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_jc = (P.ny_pad + 31) / 32;
+    const int rank = (int)cluster_ctarank();
+    const int cluster_id = blockIdx.x / P.cm, num_clusters = gridDim.x / P.cm;
+    const uint32_t b_slice = b_bytes / (uint32_t)P.cm;  // rows block_n / cm
+    const uint16_t mask = cluster_mask(P.cm);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, P.cm);  // released by the UMMA commits of every CTA of the cluster
         }
         for (int r = 0; r < R; ++r) {
             mbar_init(yfull0 + 8 * r, 1);
@@ -203,18 +218,19 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         prefetch_tensormap(&t_ay);
     }
     fence_before_sync();
-    __syncthreads();
+    cluster_sync();  // barriers of every CTA of the cluster are initialised before any multicast
     fence_after_sync();
     const uint32_t tmem_base = *tmem_slot;
 
     if (warp == 0) {
-        // operand loader
+        // operand loader: own A tile, 1/cm of the shared B rows multicast to the cluster
         if (lane == 0) {
             Ring rg;
             uint32_t issued_phase[4] = {0, 0, 0, 0};
             int issued_mask = 0;
-            for (int tile = blockIdx.x; tile < P.num_tiles && !*abort_flag; tile += gridDim.x) {
-                const int m_blk = tile / P.n_tiles, n_blk = tile % P.n_tiles;
+            for (int g = cluster_id; g < P.num_groups && !*abort_flag; g += num_clusters) {
+                const int m_blk = (g / P.n_tiles) * P.cm + rank, n_blk = g % P.n_tiles;
+                const int b_row = n_blk * P.block_n + rank * (P.block_n / P.cm);
                 for (int kb = 0; kb < P.num_kb; ++kb) {
                     if (!mbar_wait(empty0 + 8 * rg.stage, rg.phase ^ 1, abort_flag, kWaitLimitNs)) break;
                     const uint32_t sbase = smem_u32(smem + (size_t)rg.stage * stage_bytes);
@@ -222,8 +238,14 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                     mbar_arrive_expect_tx(fb, stage_bytes);
                     tma_load_2d(sbase, &ta_hi, fb, kb * kTcBlockK, m_blk * kTcBlockM);
                     tma_load_2d(sbase + kTileBytesA, &ta_lo, fb, kb * kTcBlockK, m_blk * kTcBlockM);
-                    tma_load_2d(sbase + 2 * kTileBytesA, &tb_hi, fb, kb * kTcBlockK, n_blk * P.block_n);
-                    tma_load_2d(sbase + 2 * kTileBytesA + b_bytes, &tb_lo, fb, kb * kTcBlockK, n_blk * P.block_n);
+                    const uint32_t bh = sbase + 2 * kTileBytesA + rank * b_slice;
+                    if (P.cm > 1) {
+                        tma_load_2d_multicast(bh, &tb_hi, fb, kb * kTcBlockK, b_row, mask);
+                        tma_load_2d_multicast(bh + b_bytes, &tb_lo, fb, kb * kTcBlockK, b_row, mask);
+                    } else {
+                        tma_load_2d(bh, &tb_hi, fb, kb * kTcBlockK, b_row);
+                        tma_load_2d(bh + b_bytes, &tb_lo, fb, kb * kTcBlockK, b_row);
+                    }
                     issued_phase[rg.stage] = rg.phase;
                     issued_mask |= 1 << rg.stage;
                     rg.next(S);
@@ -240,7 +262,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             Ring rg;
             int lt = 0;
             bool issued_any = false;
-            for (int tile = blockIdx.x; tile < P.num_tiles; tile += gridDim.x, ++lt) {
+            for (int g = cluster_id; g < P.num_groups; g += num_clusters, ++lt) {
                 const int a = lt & 1;
                 const uint32_t ap = (lt >> 1) & 1;
                 if (!mbar_wait(tempty0 + 8 * a, ap ^ 1, abort_flag, kWaitLimitNs)) break;
@@ -267,13 +289,19 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                         umma_f16(d_tmem, dal, dbh, idesc, 1u);
                     }
                     issued_any = true;
-                    umma_commit(empty0 + 8 * rg.stage);
+                    // the stage is free only when every CTA of the cluster has consumed it
+                    if (P.cm > 1)
+                        umma_commit_multicast(empty0 + 8 * rg.stage, mask);
+                    else
+                        umma_commit(empty0 + 8 * rg.stage);
                     rg.next(S);
                 }
                 if (!ok) break;
                 umma_commit(tfull0 + 8 * a);
             }
-            if (*abort_flag && issued_any) {
+            // all UMMAs and their commits (some arrive in other CTAs) have
+            // landed before the block leaves the cluster barrier below
+            if (issued_any) {
                 umma_commit(fin);
                 drain_wait(fin, 0);
             }
@@ -284,8 +312,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             Ring rg;
             uint32_t issued_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             int issued_mask = 0;
-            for (int tile = blockIdx.x; tile < P.num_tiles && !*abort_flag; tile += gridDim.x) {
-                const int m_blk = tile / P.n_tiles;
+            for (int g = cluster_id; g < P.num_groups && !*abort_flag; g += num_clusters) {
+                const int m_blk = (g / P.n_tiles) * P.cm + rank;
                 for (int jc = 0; jc < n_jc; ++jc) {
                     if (!mbar_wait(yempty0 + 8 * rg.stage, rg.phase ^ 1, abort_flag, kWaitLimitNs)) break;
                     const uint32_t yb = yfull0 + 8 * rg.stage;
@@ -309,12 +337,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
         Ring yr;
         int lt = 0;
-        for (int tile = blockIdx.x; tile < P.num_tiles; tile += gridDim.x, ++lt) {
+        for (int g = cluster_id; g < P.num_groups; g += num_clusters, ++lt) {
             const int a = lt & 1;
             const uint32_t ap = (lt >> 1) & 1;
             if (!mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) break;
             fence_after_sync();
-            const int m_blk = tile / P.n_tiles, n_blk = tile % P.n_tiles;
+            const int m_blk = (g / P.n_tiles) * P.cm + rank, n_blk = g % P.n_tiles;
             float s0[kMaxCoilsPerTile], s1[kMaxCoilsPerTile];
 #pragma unroll
             for (int cs = 0; cs < kMaxCoilsPerTile; ++cs) s0[cs] = s1[cs] = 0.f;
@@ -324,32 +352,36 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                     ok = false;
                     break;
                 }
-                // A_y[k][j] of this thread's sample at column j = 32 jc + q: smem [q][k_local]
+                // A_y[k][j] of this thread's sample at column j = 32 jc + q: smem [q][k_local];
+                // read once per chunk, used by every coil of the tile.  The Re
+                // row (o = 0) needs (Re, Im) of A_y, the Im row (-Im, Re).
                 const float2 *ay = reinterpret_cast<const float2 *>(ay_ring + (size_t)yr.stage * kAyChunkBytes) +
                                    kk_local;
+                float c0[32], c1[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const float2 w = ay[q * 64];
+                    c0[q] = o ? -w.y : w.x;
+                    c1[q] = o ? w.x : w.y;
+                }
                 const bool full32 = P.ny_pad - 32 * jc >= 32;
 #pragma unroll
                 for (int cs = 0; cs < kMaxCoilsPerTile; ++cs) {
                     if (cs < P.cpt) {
                         const uint32_t col = (uint32_t)(a * P.block_n + cs * P.ny_pad + 32 * jc);
+                        float v[32];
                         if (full32) {
-                            float v[32];
                             tmem_ld_32cols(tmem_base + lane_base + col, v);
-#pragma unroll
-                            for (int q = 0; q < 32; ++q) {
-                                const float2 w = ay[q * 64];
-                                s0[cs] = fmaf(v[q], o ? -w.y : w.x, s0[cs]);
-                                s1[cs] = fmaf(v[q], o ? w.x : w.y, s1[cs]);
-                            }
                         } else {
-                            float v[16];
-                            tmem_ld_16cols(tmem_base + lane_base + col, v);
+                            float v16[16];
+                            tmem_ld_16cols(tmem_base + lane_base + col, v16);
 #pragma unroll
-                            for (int q = 0; q < 16; ++q) {
-                                const float2 w = ay[q * 64];
-                                s0[cs] = fmaf(v[q], o ? -w.y : w.x, s0[cs]);
-                                s1[cs] = fmaf(v[q], o ? w.x : w.y, s1[cs]);
-                            }
+                            for (int q = 0; q < 32; ++q) v[q] = q < 16 ? v16[q] : 0.f;
+                        }
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            s0[cs] = fmaf(v[q], c0[q], s0[cs]);
+                            s1[cs] = fmaf(v[q], c1[q], s1[cs]);
                         }
                     }
                 }
@@ -379,6 +411,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         tmem_dealloc(tmem_base, P.tmem_cols);
     }
     if (threadIdx.x == 0 && *abort_flag) atomicExch(P.status, kStatusTimeout);
+    cluster_sync();  // no CTA leaves while a peer may still multicast into it or arrive on its barriers
 }
 
 // ---------------------------------------------------------------------------
@@ -402,15 +435,22 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
     uint32_t *tmem_slot = (uint32_t *)(bars + 2 * S + 2 * R + 5);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rank = (int)cluster_ctarank();
+    const int cluster_id = blockIdx.x / P.cm, num_clusters = gridDim.x / P.cm;
+    const uint32_t b_slice = b_bytes / (uint32_t)P.cm;  // rows ny_pad / cm
+    const uint16_t mask = cluster_mask(P.cm);
+    // unit u of group g: split p = u / m_tiles, tile m = u % m_tiles with the
+    // coil fastest (m = ib * nc + c); m_tiles is a multiple of cm, so all
+    // units of a group share the split and hence the B (conj A_y) rows
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(full0 + 8 * s, 129);  // 128 producer threads + the B loads' expect_tx arrival
-            mbar_init(empty0 + 8 * s, 1);
+            mbar_init(full0 + 8 * s, kAdjProducers + 1);  // producer threads + the B loads' expect_tx arrival
+            mbar_init(empty0 + 8 * s, P.cm);  // released by the UMMA commits of every CTA of the cluster
         }
         for (int r = 0; r < R; ++r) {
             mbar_init(rfull0 + 8 * r, 1);
-            mbar_init(rempty0 + 8 * r, 128);
+            mbar_init(rempty0 + 8 * r, kAdjProducers);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull0 + 8 * a, 1);
@@ -420,30 +460,33 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         *abort_flag = 0;
         fence_barrier_init();
     }
-    if (warp == 4) {
+    if (warp == kAdjMmaWarp) {
         tmem_alloc(smem_u32(tmem_slot), P.tmem_cols);
         tmem_relinquish();
     }
-    if (warp == 9 && lane == 0) {
+    if (warp == kAdjLoaderWarp && lane == 0) {
         prefetch_tensormap(&tb_hi);
         prefetch_tensormap(&tb_lo);
         prefetch_tensormap(&t_axT);
         prefetch_tensormap(&t_y);
     }
     fence_before_sync();
-    __syncthreads();
+    cluster_sync();  // barriers of every CTA of the cluster are initialised before any multicast
     fence_after_sync();
     const uint32_t tmem_base = *tmem_slot;
 
-    if (warp < 4) {
-        // producers: thread t builds, for pixel ii = t/2 and samples [16h, 16h+16)
-        // of the K block (h = t%2), the Re row 2ii and the Im row 2ii+1 of U
+    if (warp < kAdjProducerWarps) {
+        // producers: thread t builds, for pixel ii = t/4 and the eight samples
+        // [8 q4, 8 q4 + 8) of the K block (q4 = t%4), the Re row 2ii and the
+        // Im row 2ii+1 of U; two producer warps share each SM sub-partition
         const int t = threadIdx.x;
-        const int ii = t >> 1, h = t & 1;
+        const int ii = t >> 2, q4 = t & 3;
+        const int h = q4 >> 1, cbase = (q4 & 1) * 4;  // raw half and its first 16-byte chunk
         Ring rr, rs;
         uint32_t issued_phase[4] = {0, 0, 0, 0};
         int issued_mask = 0;
-        for (int u = blockIdx.x; u < P.num_units && !*abort_flag; u += gridDim.x) {
+        for (int g = cluster_id; g < P.num_groups && !*abort_flag; g += num_clusters) {
+            const int u = g * P.cm + rank;
             const int p = u / P.m_tiles;
             const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
             bool ok = true;
@@ -456,45 +499,54 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                 uint8_t *sbase = smem + (size_t)rs.stage * stage_bytes;
                 const uint32_t fb = full0 + 8 * rs.stage;
                 if (t == 0) {
-                    const uint32_t sb = smem_u32(sbase + 2 * kTileBytesA);
+                    // this CTA's 1/cm of the conj(A_y) rows, delivered to the whole cluster
+                    const uint32_t sb = smem_u32(sbase + 2 * kTileBytesA) + rank * b_slice;
+                    const int b_row = rank * (P.ny_pad / P.cm);
                     mbar_arrive_expect_tx(fb, 2u * b_bytes);
-                    tma_load_2d(sb, &tb_hi, fb, kb * kTcBlockK, 0);
-                    tma_load_2d(sb + b_bytes, &tb_lo, fb, kb * kTcBlockK, 0);
+                    if (P.cm > 1) {
+                        tma_load_2d_multicast(sb, &tb_hi, fb, kb * kTcBlockK, b_row, mask);
+                        tma_load_2d_multicast(sb + b_bytes, &tb_lo, fb, kb * kTcBlockK, b_row, mask);
+                    } else {
+                        tma_load_2d(sb, &tb_hi, fb, kb * kTcBlockK, b_row);
+                        tma_load_2d(sb + b_bytes, &tb_lo, fb, kb * kTcBlockK, b_row);
+                    }
                     issued_phase[rs.stage] = rs.phase;
                     issued_mask |= 1 << rs.stage;
                 }
                 // staged A_x^H half-row (128-byte swizzled) and y_c chunk
                 const uint8_t *arow = raw + (size_t)rr.stage * kRawBytes + h * (kRawBytes / 2) + ii * 128;
                 const float4 *yv4 = reinterpret_cast<const float4 *>(yraw + (size_t)rr.stage * kRawYBytes + h * 128);
-                float2 uval[16];
+                float2 uval[8];
 #pragma unroll
-                for (int c8 = 0; c8 < 8; ++c8) {
-                    const float4 av = *reinterpret_cast<const float4 *>(arow + ((c8 ^ (ii & 7)) << 4));
-                    const float4 yv = yv4[c8];
-                    uval[2 * c8] = cmulc(make_float2(av.x, av.y), make_float2(yv.x, yv.y));
-                    uval[2 * c8 + 1] = cmulc(make_float2(av.z, av.w), make_float2(yv.z, yv.w));
+                for (int c = 0; c < 4; ++c) {
+                    const int chunk = cbase + c;
+                    const float4 av = *reinterpret_cast<const float4 *>(arow + ((chunk ^ (ii & 7)) << 4));
+                    const float4 yv = yv4[chunk];
+                    uval[2 * c] = cmulc(make_float2(av.x, av.y), make_float2(yv.x, yv.y));
+                    uval[2 * c + 1] = cmulc(make_float2(av.z, av.w), make_float2(yv.z, yv.w));
                 }
                 mbar_arrive(rempty0 + 8 * rr.stage);
                 rr.next(R);
-                // threads with h = 0 store their Re row first and threads with
-                // h = 1 their Im row, so that each store of the warp spreads
-                // over all eight 16-byte bank groups of the swizzled tile
-                const int row_first = 2 * ii + h, row_second = 2 * ii + (h ^ 1);
+                // threads with odd q4 store their Im row first, the others their
+                // Re row, so that each store of the warp spreads over all eight
+                // 16-byte bank groups of the swizzled tile
+                const int sel = q4 & 1;
+                const int row_first = 2 * ii + sel, row_second = 2 * ii + (sel ^ 1);
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
+                for (int cc = 0; cc < 2; ++cc) {
                     uint32_t hr[4], lr[4], hm[4], lm[4];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) split_embed(uval[4 * cc + e], hr[e], lr[e], hm[e], lm[e]);
-                    const int colb = 64 * h + 16 * cc;
+                    const int colb = 32 * q4 + 16 * cc;
                     const uint32_t o1 = sw128_offset(row_first, colb), o2 = sw128_offset(row_second, colb);
                     const uint4 re_hi = make_uint4(hr[0], hr[1], hr[2], hr[3]);
                     const uint4 re_lo = make_uint4(lr[0], lr[1], lr[2], lr[3]);
                     const uint4 im_hi = make_uint4(hm[0], hm[1], hm[2], hm[3]);
                     const uint4 im_lo = make_uint4(lm[0], lm[1], lm[2], lm[3]);
-                    *reinterpret_cast<uint4 *>(sbase + o1) = h ? im_hi : re_hi;
-                    *reinterpret_cast<uint4 *>(sbase + kTileBytesA + o1) = h ? im_lo : re_lo;
-                    *reinterpret_cast<uint4 *>(sbase + o2) = h ? re_hi : im_hi;
-                    *reinterpret_cast<uint4 *>(sbase + kTileBytesA + o2) = h ? re_lo : im_lo;
+                    *reinterpret_cast<uint4 *>(sbase + o1) = sel ? im_hi : re_hi;
+                    *reinterpret_cast<uint4 *>(sbase + kTileBytesA + o1) = sel ? im_lo : re_lo;
+                    *reinterpret_cast<uint4 *>(sbase + o2) = sel ? re_hi : im_hi;
+                    *reinterpret_cast<uint4 *>(sbase + kTileBytesA + o2) = sel ? re_lo : im_lo;
                 }
                 fence_proxy_async_smem();
                 mbar_arrive(fb);
@@ -505,14 +557,15 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         if (t == 0 && *abort_flag)
             for (int s = 0; s < S; ++s)
                 if (issued_mask & (1 << s)) drain_wait(full0 + 8 * s, issued_phase[s]);
-    } else if (warp == 4) {
+    } else if (warp == kAdjMmaWarp) {
         // UMMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32(kTcBlockM, P.ny_pad);
             Ring rg;
             int lt = 0;
             bool issued_any = false;
-            for (int u = blockIdx.x; u < P.num_units; u += gridDim.x, ++lt) {
+            for (int g = cluster_id; g < P.num_groups; g += num_clusters, ++lt) {
+                const int u = g * P.cm + rank;
                 const int p = u / P.m_tiles;
                 const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
                 const int a = lt & 1;
@@ -541,26 +594,33 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                         umma_f16(d_tmem, dal, dbh, idesc, 1u);
                     }
                     issued_any = true;
-                    umma_commit(empty0 + 8 * rg.stage);
+                    // the stage is free only when every CTA of the cluster has consumed it
+                    if (P.cm > 1)
+                        umma_commit_multicast(empty0 + 8 * rg.stage, mask);
+                    else
+                        umma_commit(empty0 + 8 * rg.stage);
                     rg.next(S);
                 }
                 if (!ok) break;
                 umma_commit(tfull0 + 8 * a);
             }
-            if (*abort_flag && issued_any) {
+            // all UMMAs and their commits (some arrive in other CTAs) have
+            // landed before the block leaves the cluster barrier below
+            if (issued_any) {
                 umma_commit(fin);
                 drain_wait(fin, 0);
             }
         }
-    } else if (warp == 9) {
+    } else if (warp == kAdjLoaderWarp) {
         // loader of the A_x^H tiles (two 128-byte-swizzled halves) and the y_c chunks
         if (lane == 0) {
             Ring rg;
             uint32_t issued_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             int issued_mask = 0;
-            for (int u = blockIdx.x; u < P.num_units && !*abort_flag; u += gridDim.x) {
+            for (int g = cluster_id; g < P.num_groups && !*abort_flag; g += num_clusters) {
+                const int u = g * P.cm + rank;
                 const int p = u / P.m_tiles, m = u % P.m_tiles;
-                const int c = m / P.tiles_per_coil, ib = m % P.tiles_per_coil;
+                const int c = m % P.nc, ib = m / P.nc;
                 const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
                 for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(rempty0 + 8 * rg.stage, rg.phase ^ 1, abort_flag, kWaitLimitNs)) break;
@@ -580,19 +640,20 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                     if (issued_mask & (1 << r)) drain_wait(rfull0 + 8 * r, issued_phase[r]);
         }
     } else {
-        // epilogue: warps 5..8; TMEM lane quadrant = warp % 4
+        // epilogue: warps 9..12; TMEM lane quadrant = warp % 4
         const int wq = warp & 3;
         const int row = wq * 32 + lane;
         const int ii = row >> 1, o = row & 1;
         const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
         int lt = 0;
-        for (int u = blockIdx.x; u < P.num_units; u += gridDim.x, ++lt) {
+        for (int g = cluster_id; g < P.num_groups; g += num_clusters, ++lt) {
+            const int u = g * P.cm + rank;
             const int a = lt & 1;
             const uint32_t ap = (lt >> 1) & 1;
             if (!mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) break;
             fence_after_sync();
             const int p = u / P.m_tiles, m = u % P.m_tiles;
-            const int c = m / P.tiles_per_coil, ib = m % P.tiles_per_coil;
+            const int c = m % P.nc, ib = m / P.nc;
             const int i = ib * 64 + ii;
             float *dst = reinterpret_cast<float *>(P.part + ((size_t)p * P.nc + c) * P.ny * P.nx_pad) + 2 * i + o;
             const size_t jstride = 2 * (size_t)P.nx_pad;
@@ -619,11 +680,12 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
 
     fence_before_sync();
     __syncthreads();
-    if (warp == 4) {
+    if (warp == kAdjMmaWarp) {
         fence_after_sync();
         tmem_dealloc(tmem_base, P.tmem_cols);
     }
     if (threadIdx.x == 0 && *abort_flag) atomicExch(P.status, kStatusTimeout);
+    cluster_sync();  // no CTA leaves while a peer may still multicast into it or arrive on its barriers
 }
 
 // ---------------------------------------------------------------------------
@@ -753,10 +815,6 @@ int tc_make_tensor_maps(mri_plan *p) {
     const uint64_t nkf = 2ull * p->nk_pad;  // floats per sample-indexed row
     bool ok = make_bf16_map(&p->tm_afwd_hi, p->afwd_hi, p->kx, 2ull * p->nk, kTcBlockM) &&
               make_bf16_map(&p->tm_afwd_lo, p->afwd_lo, p->kx, 2ull * p->nk, kTcBlockM) &&
-              make_bf16_map(&p->tm_bfwd_hi, p->bfwd_hi, p->kx, (uint64_t)p->nc * p->ny_pad, p->fwd_block_n) &&
-              make_bf16_map(&p->tm_bfwd_lo, p->bfwd_lo, p->kx, (uint64_t)p->nc * p->ny_pad, p->fwd_block_n) &&
-              make_bf16_map(&p->tm_badj_hi, p->badj_hi, p->kk, p->ny_pad, p->ny_pad) &&
-              make_bf16_map(&p->tm_badj_lo, p->badj_lo, p->kk, p->ny_pad, p->ny_pad) &&
               make_map(&p->tm_axT, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->axT, nkf, p->nx, 32, 64,
                        CU_TENSOR_MAP_SWIZZLE_128B) &&
               make_map(&p->tm_y, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->y, nkf, p->nc, 64, 1,
@@ -774,6 +832,88 @@ int tc_make_tensor_maps(mri_plan *p) {
         set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
         return MRI_ERR_CUDA;
     }
+    // default cluster sizes: 2 where the shape allows (multicast halves the
+    // shared-operand traffic and clusters of two pack the GPCs densely)
+    return tc_set_clusters(p, tc_cluster_valid_fwd(p, 2) ? 2 : 1, tc_cluster_valid_adj(p, 2) ? 2 : 1);
+}
+
+namespace {
+
+template <typename Kern, typename... Args>
+cudaError_t launch_clustered(Kern kernel, int grid, int block, size_t smem, int cm, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cm;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Clusters of size cm that can be resident at once (each CTA needs an SM).
+template <typename Kern>
+int resident_clusters(Kern kernel, int block, size_t smem, int cm, int num_sms) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cm * std::max(1, num_sms / cm));
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cm;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = num_sms / cm;
+    }
+    return std::max(1, std::min(n, num_sms / cm));
+}
+
+}  // namespace
+
+bool tc_cluster_valid_fwd(const mri_plan *p, int cm) {
+    if (cm != 1 && cm != 2 && cm != 4 && cm != 8) return false;
+    return cm == 1 || (p->fwd_block_n % (8 * cm) == 0 && cm <= p->num_sms);
+}
+
+bool tc_cluster_valid_adj(const mri_plan *p, int cm) {
+    if (cm != 1 && cm != 2 && cm != 4 && cm != 8) return false;
+    return cm == 1 || (p->adj_m_tiles % cm == 0 && p->ny_pad % (8 * cm) == 0 && cm <= p->num_sms);
+}
+
+int tc_set_clusters(mri_plan *p, int fwd_cm, int adj_cm) {
+    if (fwd_cm == 0) fwd_cm = p->fwd_cluster;
+    if (adj_cm == 0) adj_cm = p->adj_cluster;
+    if (!tc_cluster_valid_fwd(p, fwd_cm) || !tc_cluster_valid_adj(p, adj_cm)) {
+        set_error("cluster size not valid for this shape");
+        return MRI_ERR_INVALID;
+    }
+    // the shared B operand is fetched in cm row slices, one per CTA of the cluster
+    bool ok = make_bf16_map(&p->tm_bfwd_hi, p->bfwd_hi, p->kx, (uint64_t)p->nc * p->ny_pad, p->fwd_block_n / fwd_cm) &&
+              make_bf16_map(&p->tm_bfwd_lo, p->bfwd_lo, p->kx, (uint64_t)p->nc * p->ny_pad, p->fwd_block_n / fwd_cm) &&
+              make_bf16_map(&p->tm_badj_hi, p->badj_hi, p->kk, p->ny_pad, p->ny_pad / adj_cm) &&
+              make_bf16_map(&p->tm_badj_lo, p->badj_lo, p->kk, p->ny_pad, p->ny_pad / adj_cm);
+    if (!ok) {
+        set_error("cuTensorMapEncodeTiled failed");
+        return MRI_ERR_CUDA;
+    }
+    p->fwd_cluster = fwd_cm;
+    p->adj_cluster = adj_cm;
+    int s, r;
+    size_t fsm, asm_;
+    fwd_smem_plan(p, &s, &r, &fsm);
+    adj_smem_plan(p, &s, &r, &asm_);
+    p->fwd_grid = fwd_cm * resident_clusters(fwd_tc_kernel, kFwdThreads, fsm, fwd_cm, p->num_sms);
+    p->adj_grid = adj_cm * resident_clusters(adj_tc_kernel, kAdjThreads, asm_, adj_cm, p->num_sms);
     return MRI_OK;
 }
 
@@ -791,21 +931,22 @@ cudaError_t launch_fwd_tc(mri_plan *p, const float2 *image, const float2 *maps, 
     P.cpt = p->fwd_coils_per_tile;
     P.block_n = p->fwd_block_n;
     P.n_tiles = p->fwd_n_tiles;
-    P.num_tiles = p->fwd_m_tiles * p->fwd_n_tiles;
     P.num_kb = p->kx / kTcBlockK;
+    P.cm = p->fwd_cluster;
+    P.num_groups = ceil_div(p->fwd_m_tiles, P.cm) * p->fwd_n_tiles;
     size_t smem;
     fwd_smem_plan(p, &P.stages, &P.ay_stages, &smem);
     P.tmem_cols = tmem_cols_for(2 * p->fwd_block_n);
     P.sc = p->scal;
     P.skip = skip;
     P.status = &p->scal->status;
-    const int grid = std::min(P.num_tiles, p->num_sms);
+    const int grid = P.cm * std::min(P.num_groups, p->fwd_grid / P.cm);
     timing_begin(p, s);
-    fwd_tc_kernel<<<grid, kFwdThreads, smem, s>>>(p->tm_afwd_hi, p->tm_afwd_lo, p->tm_bfwd_hi, p->tm_bfwd_lo,
-                                                  p->tm_ayT, P);
+    cudaError_t e = launch_clustered(fwd_tc_kernel, grid, kFwdThreads, smem, P.cm, s, p->tm_afwd_hi, p->tm_afwd_lo,
+                                     p->tm_bfwd_hi, p->tm_bfwd_lo, p->tm_ayT, P);
     timing_end(p, s);
     p->launches += 2;
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
@@ -820,19 +961,21 @@ cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
     P.m_tiles = p->adj_m_tiles;
     P.kb_per_split = p->ksplit_blocks;
     P.num_kb = p->kk / kTcBlockK;
-    P.num_units = p->adj_m_tiles * p->ksplit;
+    P.cm = p->adj_cluster;
+    P.num_groups = p->adj_m_tiles * p->ksplit / P.cm;
     size_t smem;
     adj_smem_plan(p, &P.stages, &P.raw_stages, &smem);
     P.tmem_cols = tmem_cols_for(2 * p->ny_pad);
     P.sc = p->scal;
     P.skip = skip;
     P.status = &p->scal->status;
-    const int grid = std::min(P.num_units, p->num_sms);
+    const int grid = P.cm * std::min(P.num_groups, p->adj_grid / P.cm);
     timing_begin(p, s);
-    adj_tc_kernel<<<grid, kAdjThreads, smem, s>>>(p->tm_badj_hi, p->tm_badj_lo, p->tm_axT, p->tm_y, P);
+    cudaError_t e = launch_clustered(adj_tc_kernel, grid, kAdjThreads, smem, P.cm, s, p->tm_badj_hi, p->tm_badj_lo,
+                                     p->tm_axT, p->tm_y, P);
     timing_end(p, s);
     p->launches += 1;
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace mri

@@ -141,6 +141,35 @@ def test_degenerate_shapes(mr, precision):
         assert _rel(adj, oracle.adjoint(traj, y, maps)) <= OP_TOL[precision]
 
 
+def test_cluster_sizes_change_schedule_not_results(mr):
+    # the B operand is multicast within clusters of 1..8 CTAs; every cluster
+    # size must give bit-identical products (same arithmetic, same order)
+    nx, ny, nc = 128, 128, 12
+    maps, traj, x, y = _case(nx, ny, nc, 24, 256, seed=31)
+    with mr.Plan(nx, ny, nc, _dev(traj, torch.float32), "bf16x3") as plan:
+        dm, dx, dy = _dev(maps), _dev(x), _dev(y)
+        ref_f = ref_a = None
+        tried = 0
+        for cm in (1, 2, 4, 8):
+            try:
+                plan.set_clusters(cm, cm)
+            except mr.MriError:
+                continue
+            tried += 1
+            f = mr.nudft_forward(plan, dx, dm).cpu().numpy()
+            a = mr.nudft_adjoint(plan, dy, dm).cpu().numpy()
+            if ref_f is None:
+                ref_f, ref_a = f, a
+            assert np.array_equal(f, ref_f) and np.array_equal(a, ref_a), cm
+        assert tried >= 2
+        cfg = plan.autotune(repeats=2)
+        assert cfg["fwd_cluster"] in (1, 2, 4, 8) and cfg["adj_cluster"] in (1, 2, 4, 8)
+        assert np.array_equal(mr.nudft_forward(plan, dx, dm).cpu().numpy(), ref_f)
+        plan.sync_status()
+    assert _rel(ref_f, oracle.forward(traj, x, maps)) <= OP_TOL["bf16x3"]
+    assert _rel(ref_a, oracle.adjoint(traj, y, maps)) <= OP_TOL["bf16x3"]
+
+
 def test_invalid_arguments_are_rejected(mr):
     import ctypes
     lib = mr.load()
