@@ -185,7 +185,12 @@ def run_gpu(args, rank, world, local_rank):
     results = {}
     out = torch.empty((p.nx, p.ny), dtype=torch.complex64, device=dev)
     with mr.Plan(p.nx, p.ny, p.nc, traj, "bf16x3") as plan:
-        tuned = plan.autotune(repeats=5)  # set-up, outside the timed region
+        if args.clusters:  # fixed schedule (e.g. to profile the configuration a tuned run chose)
+            fc, ac = (int(v) for v in args.clusters.split(","))
+            plan.set_clusters(fc, ac)
+            tuned = plan.config()
+        else:
+            tuned = plan.autotune(repeats=5)  # set-up, outside the timed region
         gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]) \
             if os.environ.get("CUDA_VISIBLE_DEVICES") else local_rank
         with ClockSampler(gpu_index) as clk:
@@ -348,6 +353,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--clusters", default="",
+                    help="'F,A': forward and adjoint cluster sizes instead of autotuning them")
     ap.add_argument("--forms", default="bf16x3,e2e,fp32",
                     help="comma list of what to run: bf16x3 (always), e2e (host-buffer run), fp32 (plain FP32 "
                          "form); the default runs all three")

@@ -75,6 +75,7 @@ struct AdjParams {
     float2 *part;  // [ksplit][nc][ny][nx_pad]
     int nx, ny, ny_pad, nx_pad, nc, tiles_per_coil, m_tiles, kb_per_split, num_kb;
     int stages, raw_stages;
+    int n_acc, a_col0;   // accumulator buffers in TMEM; first TMEM column of the A slots
     int cm, num_groups;  // cluster size; groups = m_tiles * ksplit / cm
     uint32_t tmem_cols;
     const DevScalars *sc;
@@ -415,6 +416,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Adjoint product.  The dynamic operand U (real-embedded, hi/lo) is written by
+// the producer warps straight into tensor memory with tcgen05.st; the UMMAs
+// read it from there (A in TMEM) and only the static conj(A_y) operand goes
+// through shared memory.  TMEM columns: n_acc accumulators of ny_pad columns,
+// then `stages` A slots of 64 columns (32 hi, 32 lo) starting at a_col0.
 __global__ void __launch_bounds__(kAdjThreads, 1)
     adj_tc_kernel(const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
                   const __grid_constant__ CUtensorMap t_axT, const __grid_constant__ CUtensorMap t_y,
@@ -423,8 +429,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     const uint32_t b_bytes = (uint32_t)P.ny_pad * 128u;
-    const uint32_t stage_bytes = 2u * kTileBytesA + 2u * b_bytes;
-    const int S = P.stages, R = P.raw_stages;
+    const uint32_t stage_bytes = 2u * b_bytes;  // B hi, B lo
+    const int S = P.stages, R = P.raw_stages, NA = P.n_acc;
     uint8_t *raw = smem + (size_t)S * stage_bytes;
     uint8_t *yraw = raw + (size_t)R * kRawBytes;
     uint64_t *bars = (uint64_t *)(yraw + (size_t)R * kRawYBytes);
@@ -476,14 +482,17 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
     const uint32_t tmem_base = *tmem_slot;
 
     if (warp < kAdjProducerWarps) {
-        // producers: thread t builds, for pixel ii = t/4 and the eight samples
-        // [8 q4, 8 q4 + 8) of the K block (q4 = t%4), the Re row 2ii and the
-        // Im row 2ii+1 of U; two producer warps share each SM sub-partition
-        const int t = threadIdx.x;
-        const int ii = t >> 2, q4 = t & 3;
-        const int h = q4 >> 1, cbase = (q4 & 1) * 4;  // raw half and its first 16-byte chunk
+        // producers: warp w owns TMEM lanes [32 (w%4), 32 (w%4) + 32) and the
+        // sixteen samples [16 kh, 16 kh + 16) of each K block (kh = w/4).
+        // Lane l holds row r = 32 (w%4) + l of U's real embedding: pixel
+        // ii = r/2, Re row (o = 0) or Im row (o = 1).  The two threads of a
+        // pixel each form eight of the sixteen products and swap halves.
+        const int q = warp & 3, kh = warp >> 2;
+        const int row = 32 * q + lane;
+        const int ii = row >> 1, o = row & 1;
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         Ring rr, rs;
-        uint32_t issued_phase[4] = {0, 0, 0, 0};
+        uint32_t issued_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int issued_mask = 0;
         for (int g = cluster_id; g < P.num_groups && !*abort_flag; g += num_clusters) {
             const int u = g * P.cm + rank;
@@ -496,11 +505,10 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                     ok = false;
                     break;
                 }
-                uint8_t *sbase = smem + (size_t)rs.stage * stage_bytes;
                 const uint32_t fb = full0 + 8 * rs.stage;
-                if (t == 0) {
+                if (threadIdx.x == 0) {
                     // this CTA's 1/cm of the conj(A_y) rows, delivered to the whole cluster
-                    const uint32_t sb = smem_u32(sbase + 2 * kTileBytesA) + rank * b_slice;
+                    const uint32_t sb = smem_u32(smem + (size_t)rs.stage * stage_bytes) + rank * b_slice;
                     const int b_row = rank * (P.ny_pad / P.cm);
                     mbar_arrive_expect_tx(fb, 2u * b_bytes);
                     if (P.cm > 1) {
@@ -513,48 +521,47 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                     issued_phase[rs.stage] = rs.phase;
                     issued_mask |= 1 << rs.stage;
                 }
-                // staged A_x^H half-row (128-byte swizzled) and y_c chunk
-                const uint8_t *arow = raw + (size_t)rr.stage * kRawBytes + h * (kRawBytes / 2) + ii * 128;
-                const float4 *yv4 = reinterpret_cast<const float4 *>(yraw + (size_t)rr.stage * kRawYBytes + h * 128);
-                float2 uval[8];
+                // staged A_x^H half-row kh (128-byte swizzled) and y_c chunk:
+                // this thread's samples are chunks 4o .. 4o+3 of the half
+                const uint8_t *arow = raw + (size_t)rr.stage * kRawBytes + kh * (kRawBytes / 2) + ii * 128;
+                const float4 *yv4 =
+                    reinterpret_cast<const float4 *>(yraw + (size_t)rr.stage * kRawYBytes + kh * 128);
+                uint32_t hre[8], lre[8], him[8], lim[8];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const int chunk = cbase + c;
+                    const int chunk = 4 * o + c;
                     const float4 av = *reinterpret_cast<const float4 *>(arow + ((chunk ^ (ii & 7)) << 4));
                     const float4 yv = yv4[chunk];
-                    uval[2 * c] = cmulc(make_float2(av.x, av.y), make_float2(yv.x, yv.y));
-                    uval[2 * c + 1] = cmulc(make_float2(av.z, av.w), make_float2(yv.z, yv.w));
+                    split_embed(cmulc(make_float2(av.x, av.y), make_float2(yv.x, yv.y)), hre[2 * c], lre[2 * c],
+                                him[2 * c], lim[2 * c]);
+                    split_embed(cmulc(make_float2(av.z, av.w), make_float2(yv.z, yv.w)), hre[2 * c + 1],
+                                lre[2 * c + 1], him[2 * c + 1], lim[2 * c + 1]);
                 }
                 mbar_arrive(rempty0 + 8 * rr.stage);
                 rr.next(R);
-                // threads with odd q4 store their Im row first, the others their
-                // Re row, so that each store of the warp spreads over all eight
-                // 16-byte bank groups of the swizzled tile
-                const int sel = q4 & 1;
-                const int row_first = 2 * ii + sel, row_second = 2 * ii + (sel ^ 1);
+                // the Re-row thread keeps its Re words and receives the
+                // partner's; the Im-row thread likewise, in sample order
+                uint32_t hi[16], lo[16];
 #pragma unroll
-                for (int cc = 0; cc < 2; ++cc) {
-                    uint32_t hr[4], lr[4], hm[4], lm[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) split_embed(uval[4 * cc + e], hr[e], lr[e], hm[e], lm[e]);
-                    const int colb = 32 * q4 + 16 * cc;
-                    const uint32_t o1 = sw128_offset(row_first, colb), o2 = sw128_offset(row_second, colb);
-                    const uint4 re_hi = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-                    const uint4 re_lo = make_uint4(lr[0], lr[1], lr[2], lr[3]);
-                    const uint4 im_hi = make_uint4(hm[0], hm[1], hm[2], hm[3]);
-                    const uint4 im_lo = make_uint4(lm[0], lm[1], lm[2], lm[3]);
-                    *reinterpret_cast<uint4 *>(sbase + o1) = sel ? im_hi : re_hi;
-                    *reinterpret_cast<uint4 *>(sbase + kTileBytesA + o1) = sel ? im_lo : re_lo;
-                    *reinterpret_cast<uint4 *>(sbase + o2) = sel ? re_hi : im_hi;
-                    *reinterpret_cast<uint4 *>(sbase + kTileBytesA + o2) = sel ? re_lo : im_lo;
+                for (int e = 0; e < 8; ++e) {
+                    const uint32_t rh = __shfl_xor_sync(0xffffffffu, o ? hre[e] : him[e], 1);
+                    const uint32_t rl = __shfl_xor_sync(0xffffffffu, o ? lre[e] : lim[e], 1);
+                    hi[e] = o ? rh : hre[e];
+                    lo[e] = o ? rl : lre[e];
+                    hi[8 + e] = o ? him[e] : rh;
+                    lo[8 + e] = o ? lim[e] : rl;
                 }
-                fence_proxy_async_smem();
+                const uint32_t acol = (uint32_t)(P.a_col0 + 64 * rs.stage + 16 * kh);
+                tmem_st_16cols(tmem_base + lane_base + acol, hi);
+                tmem_st_16cols(tmem_base + lane_base + acol + 32, lo);
+                tmem_wait_st();
+                fence_before_sync();
                 mbar_arrive(fb);
                 rs.next(S);
             }
             if (!ok) break;
         }
-        if (t == 0 && *abort_flag)
+        if (threadIdx.x == 0 && *abort_flag)
             for (int s = 0; s < S; ++s)
                 if (issued_mask & (1 << s)) drain_wait(full0 + 8 * s, issued_phase[s]);
     } else if (warp == kAdjMmaWarp) {
@@ -568,8 +575,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                 const int u = g * P.cm + rank;
                 const int p = u / P.m_tiles;
                 const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
-                const int a = lt & 1;
-                const uint32_t ap = (lt >> 1) & 1;
+                const int a = lt % NA;
+                const uint32_t ap = (lt / NA) & 1;
                 if (!mbar_wait(tempty0 + 8 * a, ap ^ 1, abort_flag, kWaitLimitNs)) break;
                 fence_after_sync();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(a * P.ny_pad);
@@ -580,18 +587,16 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                         break;
                     }
                     fence_after_sync();
-                    const uint32_t sa_hi = smem_u32(smem + (size_t)rg.stage * stage_bytes);
-                    const uint32_t sa_lo = sa_hi + kTileBytesA;
-                    const uint32_t sb_hi = sa_hi + 2 * kTileBytesA;
+                    const uint32_t ta_hi = tmem_base + (uint32_t)(P.a_col0 + 64 * rg.stage);
+                    const uint32_t ta_lo = ta_hi + 32;
+                    const uint32_t sb_hi = smem_u32(smem + (size_t)rg.stage * stage_bytes);
                     const uint32_t sb_lo = sb_hi + b_bytes;
 #pragma unroll
                     for (int kk = 0; kk < kTcBlockK / 16; ++kk) {
-                        const uint32_t off = kk * 32;
-                        const uint64_t dah = sdesc_kmajor_sw128(sa_hi + off), dal = sdesc_kmajor_sw128(sa_lo + off);
-                        const uint64_t dbh = sdesc_kmajor_sw128(sb_hi + off), dbl = sdesc_kmajor_sw128(sb_lo + off);
-                        umma_f16(d_tmem, dah, dbh, idesc, (kb != kb0 || kk != 0) ? 1u : 0u);
-                        umma_f16(d_tmem, dah, dbl, idesc, 1u);
-                        umma_f16(d_tmem, dal, dbh, idesc, 1u);
+                        const uint64_t dbh = sdesc_kmajor_sw128(sb_hi + kk * 32), dbl = sdesc_kmajor_sw128(sb_lo + kk * 32);
+                        umma_f16_tmem_a(d_tmem, ta_hi + 8 * kk, dbh, idesc, (kb != kb0 || kk != 0) ? 1u : 0u);
+                        umma_f16_tmem_a(d_tmem, ta_hi + 8 * kk, dbl, idesc, 1u);
+                        umma_f16_tmem_a(d_tmem, ta_lo + 8 * kk, dbh, idesc, 1u);
                     }
                     issued_any = true;
                     // the stage is free only when every CTA of the cluster has consumed it
@@ -648,8 +653,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         int lt = 0;
         for (int g = cluster_id; g < P.num_groups; g += num_clusters, ++lt) {
             const int u = g * P.cm + rank;
-            const int a = lt & 1;
-            const uint32_t ap = (lt >> 1) & 1;
+            const int a = lt % NA;
+            const uint32_t ap = (lt / NA) & 1;
             if (!mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) break;
             fence_after_sync();
             const int p = u / P.m_tiles, m = u % P.m_tiles;
@@ -741,17 +746,25 @@ void fwd_smem_plan(const mri_plan *p, int *stages, int *ay_stages, size_t *bytes
     *bytes = (size_t)kSmemSlack + (size_t)s * stage + (size_t)r * kAyChunkBytes;
 }
 
-void adj_smem_plan(const mri_plan *p, int *stages, int *raw_stages, size_t *bytes) {
-    const int stage = 2 * kTileBytesA + 2 * p->ny_pad * 128;
+void adj_smem_plan(const mri_plan *p, int *stages, int *raw_stages, size_t *bytes, int *n_acc = nullptr,
+                   int *a_col0 = nullptr) {
+    // shared memory holds the B (conj A_y) stages and the raw A_x^H / y ring;
+    // TMEM holds the accumulators and one 64-column A slot per stage
+    const int stage = 2 * p->ny_pad * 128;
     const int raw = kRawBytes + kRawYBytes;
-    // the staged A_x^H / y tiles come from L2 or HBM: prefer a deep raw ring
-    // (up to 6) over a third operand stage
-    int s = 2;
-    if (kMaxSmem - kSmemSlack - 3 * stage >= 4 * raw) s = 3;
-    int r = std::min(6, (kMaxSmem - kSmemSlack - s * stage) / raw);
+    int s = 4, r = 0, na = 2, col0 = 0;
+    for (; s >= 2; --s) {
+        na = (round_up(2 * p->ny_pad, 64) + 64 * s <= 512) ? 2 : 1;
+        col0 = round_up(na * p->ny_pad, 64);
+        if (col0 + 64 * s > 512) continue;
+        r = std::min(6, (kMaxSmem - kSmemSlack - s * stage) / raw);
+        if (r >= (s > 2 ? 3 : 2)) break;
+    }
     *stages = s;
     *raw_stages = r;
     *bytes = (size_t)kSmemSlack + (size_t)s * stage + (size_t)r * raw;
+    if (n_acc) *n_acc = na;
+    if (a_col0) *a_col0 = col0;
 }
 
 }  // namespace
@@ -964,8 +977,8 @@ cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
     P.cm = p->adj_cluster;
     P.num_groups = p->adj_m_tiles * p->ksplit / P.cm;
     size_t smem;
-    adj_smem_plan(p, &P.stages, &P.raw_stages, &smem);
-    P.tmem_cols = tmem_cols_for(2 * p->ny_pad);
+    adj_smem_plan(p, &P.stages, &P.raw_stages, &smem, &P.n_acc, &P.a_col0);
+    P.tmem_cols = tmem_cols_for(P.a_col0 + 64 * P.stages);
     P.sc = p->scal;
     P.skip = skip;
     P.status = &p->scal->status;
