@@ -201,15 +201,16 @@ MRI_API int mri_nudft_adjoint_noalloc(int nx, int ny, int nk, int nc, const floa
  * ------------------------------------------------------------------------- */
 
 /* Enable (1) or disable (0) CUDA-event timing of the two product kernels of
- * this plan (forward Eq. 1 and adjoint): every launch is bracketed by events
- * on the launching stream. */
+ * this plan (forward Eq. 1 and adjoint) and of the adjoint's reduction:
+ * every launch is bracketed by events on the launching stream. */
 MRI_API int mri_plan_set_timing(mri_plan *plan, int enable);
 
 /* Total milliseconds and launch counts of the timed forward and adjoint
- * product kernels since the last read (nullable outputs); waits for the
- * recorded events and then forgets them. */
+ * product kernels and of the adjoint's split-sum/coil-combine kernel since
+ * the last read (nullable outputs); waits for the recorded events and then
+ * forgets them. */
 MRI_API int mri_plan_read_timing(mri_plan *plan, double *fwd_ms, long long *fwd_launches, double *adj_ms,
-                                 long long *adj_launches);
+                                 long long *adj_launches, double *red_ms, long long *red_launches);
 
 /* Number of kernels this plan has enqueued since creation. */
 MRI_API long long mri_plan_launch_count(const mri_plan *plan);
@@ -229,6 +230,14 @@ MRI_API int mri_plan_get_config(const mri_plan *plan, int *fwd_cluster, int *adj
 /* Set the cluster sizes (0 keeps the current one); MRI_ERR_INVALID when a
  * size does not divide the tile shape; MRI_ERR_UNSUPPORTED on an FP32 plan. */
 MRI_API int mri_plan_set_clusters(mri_plan *plan, int fwd_cluster, int adj_cluster);
+
+/* mri_admm_reconstruct captures its whole launch sequence into a CUDA graph
+ * on first use and replays it while the stream is not the legacy default
+ * stream and the arguments (pointers, parameters) are the same; enable = 0
+ * launches kernels directly.  On by default.  A plan with timing enabled
+ * always launches directly (per-kernel events are not readable from graph
+ * replays). */
+MRI_API int mri_plan_set_graphs(mri_plan *plan, int enable);
 
 /* Autotuner: time every valid cluster size of both products on this plan's
  * shape (`repeats` launches each, default 3) and keep the fastest.

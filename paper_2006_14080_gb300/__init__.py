@@ -82,11 +82,13 @@ def load(path: str = LIB_PATH):
         "mri_nudft_adjoint_noalloc": ([I, I, I, I, P, P, P, P, P], I),
         "mri_plan_set_timing": ([P, I], I),
         "mri_plan_read_timing": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
+                                  ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
                                   ctypes.POINTER(ctypes.c_longlong)], I),
         "mri_plan_launch_count": ([P], ctypes.c_longlong),
         "mri_plan_get_config": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "mri_plan_set_clusters": ([P, I, I], I),
         "mri_plan_autotune": ([P, I, P], I),
+        "mri_plan_set_graphs": ([P, I], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -156,12 +158,14 @@ class Plan:
         _check(load().mri_plan_set_timing(self.handle, int(bool(enable))))
 
     def read_timing(self):
-        """``{"fwd_ms", "fwd_launches", "adj_ms", "adj_launches"}`` since the last read."""
-        fm, am = ctypes.c_double(), ctypes.c_double()
-        fn, an = ctypes.c_longlong(), ctypes.c_longlong()
+        """``{"fwd_ms", "fwd_launches", "adj_ms", "adj_launches", "red_ms", "red_launches"}``
+        since the last read."""
+        fm, am, rm = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        fn, an, rn = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
         _check(load().mri_plan_read_timing(self.handle, ctypes.byref(fm), ctypes.byref(fn), ctypes.byref(am),
-                                           ctypes.byref(an)))
-        return {"fwd_ms": fm.value, "fwd_launches": fn.value, "adj_ms": am.value, "adj_launches": an.value}
+                                           ctypes.byref(an), ctypes.byref(rm), ctypes.byref(rn)))
+        return {"fwd_ms": fm.value, "fwd_launches": fn.value, "adj_ms": am.value, "adj_launches": an.value,
+                "red_ms": rm.value, "red_launches": rn.value}
 
     def launch_count(self) -> int:
         return int(load().mri_plan_launch_count(self.handle))
@@ -171,6 +175,10 @@ class Plan:
         _check(load().mri_plan_get_config(self.handle, *[ctypes.byref(q) for q in v]))
         return {"fwd_cluster": v[0].value, "adj_cluster": v[1].value, "adj_ksplit": v[2].value,
                 "fwd_coils_per_tile": v[3].value}
+
+    def set_graphs(self, enable: bool = True):
+        """Capture/replay whole reconstructions as CUDA graphs (default on)."""
+        _check(load().mri_plan_set_graphs(self.handle, int(bool(enable))))
 
     def set_clusters(self, fwd: int = 0, adj: int = 0):
         _check(load().mri_plan_set_clusters(self.handle, int(fwd), int(adj)))

@@ -16,6 +16,14 @@ static thread_local std::string g_last_error;
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
+void invalidate_graph(mri_plan *p) {
+    if (p->graph_exec) {
+        cudaGraphExecDestroy(p->graph_exec);
+        p->graph_exec = nullptr;
+    }
+    p->graph_launches = 0;
+}
+
 namespace {
 
 int fail(int code, const std::string &msg) {
@@ -52,13 +60,14 @@ int dev_alloc(mri_plan *p, T **ptr, size_t count) {
 
 void free_plan(mri_plan *p) {
     if (!p) return;
+    invalidate_graph(p);
     void *bufs[] = {p->ax,  p->ay,  p->axT,  p->ayT,   p->afwd_hi, p->afwd_lo, p->badj_hi, p->badj_lo,
                     p->bfwd_hi, p->bfwd_lo, p->bsx, p->y, p->part, p->x, p->xprev, p->r,
                     p->d,   p->ad,  p->b,    p->fhd,   p->mu,      p->eta,     p->partials, p->scal};
     for (void *q : bufs)
         if (q) cudaFree(q);
     for (cudaEvent_t e : p->ev_free) cudaEventDestroy(e);
-    for (auto *list : {&p->ev_fwd, &p->ev_adj})
+    for (auto *list : {&p->ev_fwd, &p->ev_adj, &p->ev_red})
         for (auto &pr : *list) {
             cudaEventDestroy(pr.first);
             cudaEventDestroy(pr.second);
@@ -150,7 +159,14 @@ static cudaError_t op_normal(mri_plan *p, const float2 *src, const float2 *maps,
     ep.dot_src = cg_dot ? src : nullptr;
     ep.skip = skip;
     p->launches += 1;
-    return launch_adj_reduce(p, maps, out, ep, s);
+    const bool timed = timing_arm(p);
+    if (timed) cudaEventRecord(p->t_ev0, s);
+    e = launch_adj_reduce(p, maps, out, ep, s);
+    if (timed) {
+        cudaEventRecord(p->t_ev1, s);
+        timing_disarm(p, p->ev_red);
+    }
+    return e;
 }
 
 }  // namespace mri
@@ -350,16 +366,9 @@ MRI_API int mri_soft_threshold(int n, float t, const mri_c64 *in, mri_c64 *out, 
     return MRI_OK;
 }
 
-MRI_API int mri_admm_reconstruct(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in,
-                                 const mri_admm_params *prm, mri_c64 *image_out, double *objective_hist,
-                                 double *alpha_hist, mri_stream_t stream) {
-    if (!p || !kspace_in || !maps_in || !prm || !image_out) return fail(MRI_ERR_INVALID, "null argument");
-    if (!finite(prm->lambda) || prm->lambda < 0.f) return fail(MRI_ERR_INVALID, "lambda must be finite and >= 0");
-    if (!finite(prm->beta) || !(prm->beta > 0.f)) return fail(MRI_ERR_INVALID, "beta must be finite and > 0");
-    if (prm->admm_iters < 0 || prm->cg_iters < 0) return fail(MRI_ERR_INVALID, "iteration counts must be >= 0");
-    if (!isfinite(prm->rtol) || prm->rtol < 0 || !isfinite(prm->atol) || prm->atol < 0)
-        return fail(MRI_ERR_INVALID, "tolerances must be finite and >= 0");
-    cudaStream_t s = (cudaStream_t)stream;
+// Enqueue the whole reconstruction (Alg. 4 with Alg. 2) on s.
+static int enqueue_admm(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in, const mri_admm_params *prm,
+                        mri_c64 *image_out, double *objective_hist, double *alpha_hist, cudaStream_t s) {
     const float2 *kspace = (const float2 *)kspace_in;
     const float2 *maps = (const float2 *)maps_in;
     const size_t npix = (size_t)p->nx * p->ny;
@@ -406,6 +415,61 @@ MRI_API int mri_admm_reconstruct(mri_plan *p, const mri_c64 *kspace_in, const mr
     return MRI_OK;
 }
 
+MRI_API int mri_admm_reconstruct(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in,
+                                 const mri_admm_params *prm, mri_c64 *image_out, double *objective_hist,
+                                 double *alpha_hist, mri_stream_t stream) {
+    if (!p || !kspace_in || !maps_in || !prm || !image_out) return fail(MRI_ERR_INVALID, "null argument");
+    if (!finite(prm->lambda) || prm->lambda < 0.f) return fail(MRI_ERR_INVALID, "lambda must be finite and >= 0");
+    if (!finite(prm->beta) || !(prm->beta > 0.f)) return fail(MRI_ERR_INVALID, "beta must be finite and > 0");
+    if (prm->admm_iters < 0 || prm->cg_iters < 0) return fail(MRI_ERR_INVALID, "iteration counts must be >= 0");
+    if (!isfinite(prm->rtol) || prm->rtol < 0 || !isfinite(prm->atol) || prm->atol < 0)
+        return fail(MRI_ERR_INVALID, "tolerances must be finite and >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    // per-kernel timing events cannot be read back from graph replays, so a
+    // timed plan launches its kernels directly
+    if (!p->use_graphs || s == nullptr || p->timing)
+        return enqueue_admm(p, kspace_in, maps_in, prm, image_out, objective_hist, alpha_hist, s);
+    const mri_plan::GraphKey key{kspace_in, maps_in,         image_out,     objective_hist, alpha_hist,
+                                 prm->lambda, prm->beta, prm->admm_iters, prm->cg_iters, prm->rtol, prm->atol};
+    if (p->graph_exec && p->graph_key == key) {
+        cudaError_t e = cudaGraphLaunch(p->graph_exec, s);
+        if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+        p->launches += p->graph_launches;
+        return MRI_OK;
+    }
+    invalidate_graph(p);
+    const long long l0 = p->launches;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    const int rc = enqueue_admm(p, kspace_in, maps_in, prm, image_out, objective_hist, alpha_hist, s);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(s, &graph);
+    if (rc != MRI_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        p->launches = l0;
+        return rc != MRI_OK ? rc : cuda_fail(e, "graph capture");
+    }
+    e = cudaGraphInstantiate(&p->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        p->graph_exec = nullptr;
+        p->launches = l0;
+        return cuda_fail(e, "graph instantiate");
+    }
+    p->graph_key = key;
+    p->graph_launches = p->launches - l0;
+    e = cudaGraphLaunch(p->graph_exec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    return MRI_OK;
+}
+
+MRI_API int mri_plan_set_graphs(mri_plan *p, int enable) {
+    if (!p) return fail(MRI_ERR_INVALID, "null plan");
+    p->use_graphs = enable != 0;
+    if (!p->use_graphs) invalidate_graph(p);
+    return MRI_OK;
+}
+
 MRI_API int mri_plan_set_timing(mri_plan *p, int enable) {
     if (!p) return fail(MRI_ERR_INVALID, "null plan");
     p->timing = enable != 0;
@@ -413,12 +477,12 @@ MRI_API int mri_plan_set_timing(mri_plan *p, int enable) {
 }
 
 MRI_API int mri_plan_read_timing(mri_plan *p, double *fwd_ms, long long *fwd_launches, double *adj_ms,
-                                 long long *adj_launches) {
+                                 long long *adj_launches, double *red_ms, long long *red_launches) {
     if (!p) return fail(MRI_ERR_INVALID, "null plan");
-    double sums[2] = {0.0, 0.0};
-    long long counts[2] = {0, 0};
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *lists[2] = {&p->ev_fwd, &p->ev_adj};
-    for (int q = 0; q < 2; ++q) {
+    double sums[3] = {0.0, 0.0, 0.0};
+    long long counts[3] = {0, 0, 0};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *lists[3] = {&p->ev_fwd, &p->ev_adj, &p->ev_red};
+    for (int q = 0; q < 3; ++q) {
         for (auto &pr : *lists[q]) {
             float ms = 0.f;
             cudaError_t e = cudaEventSynchronize(pr.second);
@@ -435,6 +499,8 @@ MRI_API int mri_plan_read_timing(mri_plan *p, double *fwd_ms, long long *fwd_lau
     if (fwd_launches) *fwd_launches = counts[0];
     if (adj_ms) *adj_ms = sums[1];
     if (adj_launches) *adj_launches = counts[1];
+    if (red_ms) *red_ms = sums[2];
+    if (red_launches) *red_launches = counts[2];
     return MRI_OK;
 }
 

@@ -104,8 +104,30 @@ struct mri_plan {
     bool timing = false;
     cudaEvent_t t_ev0 = nullptr, t_ev1 = nullptr;  // set by the caller around one product launch
     std::vector<cudaEvent_t> ev_free;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_fwd, ev_adj;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_fwd, ev_adj, ev_red;
+
+    // CUDA graph of one whole reconstruction, replayed while the arguments
+    // (device pointers and parameters) stay the same
+    bool use_graphs = true;
+    struct GraphKey {
+        const void *kspace, *maps, *image_out, *obj, *alpha;
+        float lambda, beta;
+        int admm_iters, cg_iters;
+        double rtol, atol;
+        bool operator==(const GraphKey &o) const {
+            return kspace == o.kspace && maps == o.maps && image_out == o.image_out && obj == o.obj &&
+                   alpha == o.alpha && lambda == o.lambda && beta == o.beta && admm_iters == o.admm_iters &&
+                   cg_iters == o.cg_iters && rtol == o.rtol && atol == o.atol;
+        }
+    } graph_key{};
+    cudaGraphExec_t graph_exec = nullptr;
+    long long graph_launches = 0;  // kernels in one replay
 };
+
+namespace mri {
+// Drop the cached reconstruction graph (its kernels' arguments are stale).
+void invalidate_graph(mri_plan *p);
+}  // namespace mri
 
 // Record the timing events (when set) immediately around a product kernel.
 inline void timing_begin(mri_plan *p, cudaStream_t s) {

@@ -16,8 +16,9 @@
 //   matching 64-sample x 32-column tiles of A_y staged in shared memory by a
 //   TMA warp.
 // Adjoint: W_c = U_c conj(A_y) with U_c[i][k] = conj(A_x[k][i]) y_c[k]
-//     A  = embedded U_c          built in shared memory by producer warps from
-//                                A_x^H and y tiles that a TMA warp stages
+//     A  = embedded U_c          built by producer warps from A_x^H and y tiles
+//                                that a TMA warp stages, written to tensor
+//                                memory (the UMMAs read A from TMEM)
 //     B  = conj(A_y)^T           [ny_pad][kk]      static, TMA
 //   tile: 128 rows (64 pixels of one coil) x ny_pad columns, split over
 //   contiguous k-space ranges; the epilogue writes partial images that
@@ -919,6 +920,7 @@ int tc_set_clusters(mri_plan *p, int fwd_cm, int adj_cm) {
         set_error("cuTensorMapEncodeTiled failed");
         return MRI_ERR_CUDA;
     }
+    invalidate_graph(p);  // captured launches carry the old maps and cluster sizes
     p->fwd_cluster = fwd_cm;
     p->adj_cluster = adj_cm;
     int s, r;

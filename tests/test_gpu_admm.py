@@ -111,6 +111,28 @@ def test_admm_table1_tolerances_stop_like_oracle(mr, precision):
     assert _nrmse(x, ref["x"]) <= 1e-2
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_graph_replay_matches_direct_launches(mr, precision):
+    # a side stream enables capture; the first call captures and launches the
+    # graph, the second replays it, the third (graphs off) launches directly
+    p = synth.config_small()
+    d = oracle.measurements(p)
+    side = torch.cuda.Stream()
+    outs = []
+    with torch.cuda.stream(side):
+        with mr.Plan(p.nx, p.ny, p.nc, _dev(p.traj, torch.float32), precision) as plan:
+            dk, dm = _dev(d), _dev(p.maps)
+            obj = torch.zeros(p.admm_iters, dtype=torch.float64, device="cuda")
+            for graphs in (True, True, False):
+                plan.set_graphs(graphs)
+                x = mr.admm_reconstruct(plan, dk, dm, p.lam, p.beta, p.admm_iters, p.cg_iters,
+                                        objective_hist=obj)
+                outs.append((x.cpu().numpy(), obj.cpu().numpy().copy()))
+            plan.sync_status()
+    for x, o in outs[1:]:
+        assert np.array_equal(x, outs[0][0]) and np.array_equal(o, outs[0][1])
+
+
 def test_admm_zero_iterations_returns_zero_image(mr):
     p = synth.config_small()
     d = oracle.measurements(p)
