@@ -44,8 +44,9 @@ __device__ __forceinline__ float2 theta_h_theta_at(const float2 *p, int i, int j
 // out[i][j] = sum_c conj(S_c[i][j]) sum_p part[p][c][j][i]  (+ half_beta Theta^H Theta tv_src)
 // and optionally Re<dot_src, out> -> alpha = tau / dot.  Block (32, 16)
 // covers 32 consecutive pixels i of one column j; thread row ty takes the
-// (split, coil) pairs q = ty, ty + 16, ... (reads coalesced along i, four in
-// flight), and the sixteen groups are then added in a fixed order.
+// coils c = ty, ty + 16, ..., sums each coil's k-space splits (reads
+// coalesced along i, four in flight, combined in a fixed order), applies
+// conj(S_c) once per coil, and the sixteen groups are added in a fixed order.
 constexpr int kReduceGroups = 16;
 __global__ void __launch_bounds__(32 * kReduceGroups)
     adj_reduce_kernel(const float2 *__restrict__ part, int ksplit, int nc, int nx, int ny, int nx_pad,
@@ -58,25 +59,22 @@ __global__ void __launch_bounds__(32 * kReduceGroups)
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int i = blockIdx.x * 32 + tx, j = blockIdx.y;
     const size_t npix = (size_t)nx * ny;
-    const int npairs = ksplit * nc;  // pair q = p * nc + c, stored at part + q * ny * nx_pad
     float2 acc = make_float2(0.f, 0.f);
     if (i < nx) {
-        const float2 *src = part + (size_t)j * nx_pad + i;
-        const float2 *S = maps + (size_t)i * ny + j;
-        const size_t pstride = (size_t)ny * nx_pad;
-        int q = ty;
-        for (; q + 3 * kReduceGroups < npairs; q += 4 * kReduceGroups) {
-            float2 w[4], s[4];
+        const size_t pstride = (size_t)nc * ny * nx_pad;  // between k-space splits
+        for (int c = ty; c < nc; c += kReduceGroups) {
+            const float2 *src = part + ((size_t)c * ny + j) * nx_pad + i;
+            float2 w[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
+                           make_float2(0.f, 0.f)};
+            int p = 0;
+            for (; p + 3 < ksplit; p += 4) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int qq = q + e * kReduceGroups;
-                w[e] = src[(size_t)qq * pstride];
-                s[e] = S[(size_t)(qq % nc) * npix];
+                for (int e = 0; e < 4; ++e) w[e] = cadd(w[e], src[(size_t)(p + e) * pstride]);
             }
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc = cadd(acc, cmulc(s[e], w[e]));
+            for (; p < ksplit; ++p) w[0] = cadd(w[0], src[(size_t)p * pstride]);
+            const float2 wsum = cadd(cadd(w[0], w[1]), cadd(w[2], w[3]));
+            acc = cadd(acc, cmulc(maps[c * npix + (size_t)i * ny + j], wsum));
         }
-        for (; q < npairs; q += kReduceGroups) acc = cadd(acc, cmulc(S[(size_t)(q % nc) * npix], src[(size_t)q * pstride]));
     }
     grp[ty][tx] = acc;
     __syncthreads();
