@@ -174,6 +174,44 @@ MRI_API int mri_admm_reconstruct(mri_plan *plan, const mri_c64 *kspace, const mr
                                  double *objective_hist, double *alpha_hist, mri_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched reconstructions (not in the paper, which reconstructs one image
+ * at a time): many independent problems of different shapes in one launch.
+ * ------------------------------------------------------------------------- */
+
+/* One reconstruction of a batch: its own plan (created for its shape and
+ * trajectory; plans may not be shared between requests of a batch), device
+ * inputs and output as for mri_admm_reconstruct, and its parameters. */
+typedef struct {
+    mri_plan *plan;
+    const mri_c64 *kspace;     /* [nc][nk] */
+    const mri_c64 *coil_maps;  /* [nc][nx][ny] */
+    mri_c64 *image_out;        /* [nx][ny] */
+    mri_admm_params params;
+} mri_request;
+
+typedef struct mri_batch mri_batch;
+
+/* A batch object caches the combined launch of one request list. */
+MRI_API int mri_batch_create(mri_batch **batch);
+MRI_API int mri_batch_destroy(mri_batch *batch);
+
+/*
+ * Reconstruct n independent problems (Alg. 4 each).  Every request's whole
+ * reconstruction is captured into a child CUDA graph; the children are
+ * independent nodes of one parent graph, launched with one
+ * cudaGraphLaunch on `stream`, so their kernels overlap on the GPU.  The
+ * parent graph is cached and replayed while the request list (plans,
+ * pointers, parameters) repeats.  Each result is identical to the one the
+ * request produces alone (same kernels, tiles and summation order).
+ * Requests may not use timing-enabled plans.  The first call on a request
+ * list captures (host work proportional to the number of launches).
+ */
+MRI_API int mri_batch_reconstruct(mri_batch *batch, int n, const mri_request *reqs, mri_stream_t stream);
+
+/* Kernels in one replay of the cached batch launch. */
+MRI_API long long mri_batch_launch_count(const mri_batch *batch);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free adjoint (the paper has no counterpart; it is a convenience
  * for callers that cannot allocate device memory -- code running where the
  * CUDA allocator must not be touched, such as a real-time loop, a host

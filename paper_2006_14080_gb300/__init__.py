@@ -52,6 +52,11 @@ class AdmmParams(ctypes.Structure):
                 ("cg_iters", ctypes.c_int), ("rtol", ctypes.c_double), ("atol", ctypes.c_double)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("kspace", ctypes.c_void_p), ("coil_maps", ctypes.c_void_p),
+                ("image_out", ctypes.c_void_p), ("params", AdmmParams)]
+
+
 _lib = None
 
 
@@ -89,6 +94,10 @@ def load(path: str = LIB_PATH):
         "mri_plan_set_clusters": ([P, I, I], I),
         "mri_plan_autotune": ([P, I, P], I),
         "mri_plan_set_graphs": ([P, I], I),
+        "mri_batch_create": ([ctypes.POINTER(P)], I),
+        "mri_batch_destroy": ([P], I),
+        "mri_batch_reconstruct": ([P, I, ctypes.POINTER(Request), P], I),
+        "mri_batch_launch_count": ([P], ctypes.c_longlong),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -299,3 +308,56 @@ def admm_reconstruct(plan: Plan, kspace, coil_maps, lam: float, beta: float, adm
     _check(load().mri_admm_reconstruct(plan.handle, _ptr(kspace), _ptr(coil_maps), ctypes.byref(prm), _ptr(out),
                                        _ptr(objective_hist), _ptr(alpha_hist), _stream(stream)))
     return out
+
+
+class Batch:
+    """Many independent reconstructions in one launch (``mri_batch_*``).
+
+    ``reconstruct(items)`` takes a list of dicts with keys ``plan``, ``kspace``,
+    ``coil_maps``, ``out`` (CUDA tensors as for :func:`admm_reconstruct`) and
+    ``lam``, ``beta``, ``admm_iters``, ``cg_iters`` (optional ``rtol``,
+    ``atol``).  Each item needs its own plan.  The combined launch is cached
+    while the item list repeats.
+    """
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(load().mri_batch_create(ctypes.byref(h)))
+        self._h = h
+        self._keep = None
+
+    def reconstruct(self, items, stream=None):
+        reqs = (Request * len(items))()
+        for q, it in enumerate(items):
+            plan = it["plan"]
+            _need(it["kspace"], torch.complex64, (plan.nc, plan.nk), "kspace")
+            _need(it["coil_maps"], torch.complex64, (plan.nc, plan.nx, plan.ny), "coil_maps")
+            _need(it["out"], torch.complex64, (plan.nx, plan.ny), "out")
+            reqs[q].plan = plan.handle.value
+            reqs[q].kspace = it["kspace"].data_ptr()
+            reqs[q].coil_maps = it["coil_maps"].data_ptr()
+            reqs[q].image_out = it["out"].data_ptr()
+            reqs[q].params = AdmmParams(float(it["lam"]), float(it["beta"]), int(it["admm_iters"]),
+                                        int(it["cg_iters"]), float(it.get("rtol", 0.0)), float(it.get("atol", 0.0)))
+        self._keep = items  # the cached launch refers to these tensors
+        _check(load().mri_batch_reconstruct(self._h, len(items), reqs, _stream(stream)))
+
+    def launch_count(self) -> int:
+        return int(load().mri_batch_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().mri_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -366,9 +366,11 @@ MRI_API int mri_soft_threshold(int n, float t, const mri_c64 *in, mri_c64 *out, 
     return MRI_OK;
 }
 
+}  // extern "C"
+
 // Enqueue the whole reconstruction (Alg. 4 with Alg. 2) on s.
-static int enqueue_admm(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in, const mri_admm_params *prm,
-                        mri_c64 *image_out, double *objective_hist, double *alpha_hist, cudaStream_t s) {
+int mri::enqueue_admm(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in, const mri_admm_params *prm,
+                      mri_c64 *image_out, double *objective_hist, double *alpha_hist, cudaStream_t s) {
     const float2 *kspace = (const float2 *)kspace_in;
     const float2 *maps = (const float2 *)maps_in;
     const size_t npix = (size_t)p->nx * p->ny;
@@ -415,15 +417,24 @@ static int enqueue_admm(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *ma
     return MRI_OK;
 }
 
-MRI_API int mri_admm_reconstruct(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in,
-                                 const mri_admm_params *prm, mri_c64 *image_out, double *objective_hist,
-                                 double *alpha_hist, mri_stream_t stream) {
+int mri::check_admm_args(const mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in,
+                         const mri_admm_params *prm, const mri_c64 *image_out) {
     if (!p || !kspace_in || !maps_in || !prm || !image_out) return fail(MRI_ERR_INVALID, "null argument");
     if (!finite(prm->lambda) || prm->lambda < 0.f) return fail(MRI_ERR_INVALID, "lambda must be finite and >= 0");
     if (!finite(prm->beta) || !(prm->beta > 0.f)) return fail(MRI_ERR_INVALID, "beta must be finite and > 0");
     if (prm->admm_iters < 0 || prm->cg_iters < 0) return fail(MRI_ERR_INVALID, "iteration counts must be >= 0");
     if (!isfinite(prm->rtol) || prm->rtol < 0 || !isfinite(prm->atol) || prm->atol < 0)
         return fail(MRI_ERR_INVALID, "tolerances must be finite and >= 0");
+    return MRI_OK;
+}
+
+extern "C" {
+
+MRI_API int mri_admm_reconstruct(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in,
+                                 const mri_admm_params *prm, mri_c64 *image_out, double *objective_hist,
+                                 double *alpha_hist, mri_stream_t stream) {
+    const int arc = check_admm_args(p, kspace_in, maps_in, prm, image_out);
+    if (arc != MRI_OK) return arc;
     cudaStream_t s = (cudaStream_t)stream;
     // per-kernel timing events cannot be read back from graph replays, so a
     // timed plan launches its kernels directly

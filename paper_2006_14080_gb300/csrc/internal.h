@@ -127,6 +127,12 @@ struct mri_plan {
 namespace mri {
 // Drop the cached reconstruction graph (its kernels' arguments are stale).
 void invalidate_graph(mri_plan *p);
+// Argument checks of mri_admm_reconstruct (MRI_* status, sets the error text).
+int check_admm_args(const mri_plan *p, const mri_c64 *kspace, const mri_c64 *maps, const mri_admm_params *prm,
+                    const mri_c64 *image_out);
+// Enqueue one whole reconstruction (Alg. 4 with Alg. 2) on s; MRI_* status.
+int enqueue_admm(mri_plan *p, const mri_c64 *kspace, const mri_c64 *maps, const mri_admm_params *prm,
+                 mri_c64 *image_out, double *objective_hist, double *alpha_hist, cudaStream_t s);
 }  // namespace mri
 
 // Record the timing events (when set) immediately around a product kernel.
