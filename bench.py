@@ -308,6 +308,158 @@ def run_gpu(args, rank, world, local_rank):
     return line
 
 
+def run_batch(args, rank, world, local_rank):
+    """64 heterogeneous reconstructions (N in {64..256}, 8-32 coils, 32-200
+    golden-angle spokes of 2N samples, 30 ADMM x 8 CG) in one batched launch
+    per step; each rank runs its own batch."""
+    import torch
+    import paper_2006_14080_gb300 as mr
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    torch.cuda.set_stream(torch.cuda.Stream(device=dev))
+    stream = torch.cuda.current_stream()
+    probs = [synth.batch_item(j) for j in range(args.batch_items)]
+    items, plans = [], []
+    useful = 0.0
+    for p in probs:
+        traj = torch.from_numpy(p.traj).to(dev)
+        maps = torch.from_numpy(p.maps).to(dev)
+        with mr.Plan(p.nx, p.ny, p.nc, traj, "fp32") as p32:
+            d_clean = mr.nudft_forward(p32, torch.from_numpy(p.image_true).to(dev), maps).cpu().numpy()
+        kspace = torch.from_numpy(synth.add_noise(d_clean, p.noise, p.noise_level)).to(dev)
+        plan = mr.Plan(p.nx, p.ny, p.nc, traj, "bf16x3")
+        plans.append(plan)
+        items.append({"plan": plan, "kspace": kspace, "coil_maps": maps,
+                      "out": torch.empty((p.nx, p.ny), dtype=torch.complex64, device=dev),
+                      "lam": p.lam, "beta": p.beta, "admm_iters": p.admm_iters, "cg_iters": p.cg_iters})
+        useful += normal_ops_per_recon(p) * 2 * useful_flops_per_product(p)
+    resident = sum(pl.device_bytes() for pl in plans)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    batch = mr.Batch()
+    for _ in range(max(1, args.warmup)):
+        batch.reconstruct(items)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        batch.reconstruct(items)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    launches = batch.launch_count()
+    batch.close()
+    for pl in plans:
+        pl.close()
+    if rank != 0:
+        return None
+    n = len(items)
+    return {
+        "metric": f"ADMM recon/s, batch of {n} heterogeneous reconstructions (N 64-256, 8-32 coils, 32-200 "
+                  f"golden-angle spokes x 2N, 30 ADMM x 8 CG), BF16x3, one batched graph launch per step",
+        "value": world * n * args.steps / (total_ms / 1e3), "unit": "recon/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3/f32",
+        "data": "synthetic (seeded per item)",
+        "config": {"workload": f"batch{n}_hetero_admm30x8", "items": n, "l2": "flushed between timed steps",
+                   "resident_plan_bytes": resident},
+        "useful_tflops": useful * args.steps / (total_ms / 1e3) / 1e12,
+        "gpu_launches": launches,
+    }
+
+
+def run_serve(args, rank, world, local_rank):
+    """Serving loop: heterogeneous requests (the batch item mix) arriving from
+    host memory as a Poisson process, admitted under a device-memory budget
+    and run concurrently.  A burst of all requests first measures the
+    server's capacity (also filling its plan cache); the timed pass then
+    submits the same requests at 80% of that rate.  value = requests / (last
+    completion - first submission); latency = submission to image on host."""
+    import threading
+    import torch
+    import paper_2006_14080_gb300 as mr
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    probs = [synth.batch_item(j) for j in range(args.serve_requests)]
+    reqs = []
+    for p in probs:
+        traj = torch.from_numpy(p.traj).to(dev)
+        maps = torch.from_numpy(p.maps).to(dev)
+        with mr.Plan(p.nx, p.ny, p.nc, traj, "fp32") as p32:
+            d_clean = mr.nudft_forward(p32, torch.from_numpy(p.image_true).to(dev), maps).cpu().numpy()
+        reqs.append((p.traj.astype(np.float32), synth.add_noise(d_clean, p.noise, p.noise_level).astype(np.complex64),
+                     p.maps.astype(np.complex64), p.lam, p.beta, p.admm_iters, p.cg_iters))
+    torch.cuda.synchronize()
+    budget = int(args.serve_budget_gb * (1 << 30))
+
+    def wave(srv, gaps):
+        lat, tickets = [], []
+        t0 = time.perf_counter()
+
+        def feed():
+            t_next = t0
+            for r, g in zip(reqs, gaps):
+                t_next += g
+                dt = t_next - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                tickets.append(srv.submit(*r))
+        th = threading.Thread(target=feed)
+        th.start()
+        q = 0
+        while q < len(reqs):
+            while len(tickets) <= q:
+                time.sleep(1e-4)
+            lat.append(srv.wait(tickets[q])[1])
+            q += 1
+        th.join()
+        return time.perf_counter() - t0, lat
+
+    with mr.Server(budget, max_inflight=args.serve_inflight, precision="bf16x3") as srv, \
+            ClockSampler(local_rank) as clk:
+        burst_s = 0.0
+        for _ in range(max(1, args.warmup)):
+            burst_s, _ = wave(srv, [0.0] * len(reqs))
+        rate = 0.8 * len(reqs) / burst_s
+        rng = np.random.default_rng(2020)
+        total_s, lats = 0.0, []
+        for _ in range(args.steps):
+            gaps = [0.0] + list(rng.exponential(1.0 / rate, len(reqs) - 1))
+            t, lat = wave(srv, gaps)
+            total_s += t
+            lats += lat
+        st = srv.stats()
+    lats.sort()
+    pct = lambda q: lats[min(len(lats) - 1, max(0, math.ceil(q * len(lats)) - 1))]  # noqa: E731
+    n = len(reqs) * args.steps
+    return {
+        "metric": f"served ADMM recon/s, {len(reqs)} heterogeneous requests (N 64-256, 8-32 coils, 32-200 "
+                  "golden-angle spokes x 2N, 30 ADMM x 8 CG) from host memory, Poisson arrivals at 80% of burst "
+                  "capacity, BF16x3",
+        "value": n / total_s, "unit": "recon/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3/f32", "data": "synthetic (seeded per item)",
+        "latency_ms": {"p50": pct(0.50), "p99": pct(0.99), "max": lats[-1]},
+        "burst_capacity_recon_s": len(reqs) / burst_s, "arrival_rate_recon_s": rate,
+        "config": {"workload": f"serve{len(reqs)}_poisson", "budget_bytes": budget,
+                   "max_inflight": args.serve_inflight, "peak_resident_bytes": st["peak_resident_bytes"],
+                   "timing": "host wall clock, submit to image in host memory"},
+        "clocks": clk.summary(),
+    }
+
+
 def oracle_sample(p, budget_s):
     """Time the FP64 oracle's normal operator (Eq. 11) at the workload's full
     size; one reconstruction needs normal_ops_per_recon() of them."""
@@ -365,6 +517,13 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--workload", default="n128", choices=["n128", "batch64", "serve"],
+                    help="n128: the single N=128 reconstruction (default); batch64: 64 heterogeneous "
+                         "reconstructions in one batched launch; serve: the serving loop under Poisson arrivals")
+    ap.add_argument("--batch-items", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-inflight", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=32.0)
     ap.add_argument("--clusters", default="",
                     help="'F,A': forward and adjoint cluster sizes instead of autotuning them")
     ap.add_argument("--forms", default="bf16x3,e2e,fp32",
@@ -376,6 +535,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         line = run_reference(args, rank)
+    elif args.workload == "batch64":
+        line = run_batch(args, rank, world, local_rank)
+    elif args.workload == "serve":
+        line = run_serve(args, rank, world, local_rank)
     else:
         line = run_gpu(args, rank, world, local_rank)
     if line is not None:

@@ -103,6 +103,10 @@ MRI_API int mri_plan_sync_status(mri_plan *plan, mri_stream_t stream);
 /* Bytes of device memory the plan holds. */
 MRI_API size_t mri_plan_device_bytes(const mri_plan *plan);
 
+/* Bytes mri_plan_create would allocate for this shape on the current
+ * device (0 for invalid arguments); allocates nothing. */
+MRI_API size_t mri_plan_estimate_bytes(int nx, int ny, int nk, int nc, int precision);
+
 /*
  * Forward operator F of Eq. 1-2:
  *   kspace[c][k] = sum_{i,j} coil_maps[c][i][j] image[i][j] exp(-i 2 pi (kx_k x_i + ky_k y_j))
@@ -210,6 +214,70 @@ MRI_API int mri_batch_reconstruct(mri_batch *batch, int n, const mri_request *re
 
 /* Kernels in one replay of the cached batch launch. */
 MRI_API long long mri_batch_launch_count(const mri_batch *batch);
+
+/* ---------------------------------------------------------------------------
+ * Serving loop (not in the paper): reconstruction requests arriving over
+ * time from host memory, admitted under a device-memory budget and run
+ * concurrently (continuous batching).
+ *
+ * A server owns a scheduler thread, `max_inflight` CUDA streams, a device
+ * memory pool for request buffers and a cache of plans keyed by shape and
+ * trajectory contents.  The scheduler starts the oldest waiting request
+ * (first in, first out) as soon as a stream is free and its device bytes --
+ * the plan's (mri_plan_estimate_bytes, unless an idle cached plan of the
+ * same key exists) plus its k-space, maps, trajectory and image buffers --
+ * fit under `hbm_budget_bytes` together with everything resident; idle
+ * cached plans are evicted least-recently-used to make room (eviction
+ * synchronises the device).  A request whose bytes exceed the whole budget
+ * fails with MRI_ERR_NOMEM; one whose shape the precision does not support
+ * fails with MRI_ERR_NOMEM too (estimate 0).  Every request runs Alg. 4
+ * with its own plan and buffers, so its image is bit-identical to the one
+ * mri_admm_reconstruct produces for it alone with a plan of the same
+ * precision and cluster sizes, whatever else is in flight.
+ * ------------------------------------------------------------------------- */
+
+typedef struct mri_server mri_server;
+
+/* One request: shape, HOST arrays (copied at submit; the caller may reuse
+ * them as soon as mri_server_submit returns) and parameters.
+ * traj [nk][2] float in cycles/pixel, kspace [nc][nk], coil_maps [nc][nx][ny]. */
+typedef struct {
+    int nx, ny, nk, nc;
+    const float *traj;
+    const mri_c64 *kspace;
+    const mri_c64 *coil_maps;
+    mri_admm_params params;
+} mri_server_request;
+
+/* Start a server on the current device.  precision: MRI_FP32 or
+ * MRI_BF16X3 for all its plans; max_inflight in 1..64. */
+MRI_API int mri_server_create(mri_server **server, size_t hbm_budget_bytes, int max_inflight, int precision);
+
+/* Queue a request; *ticket identifies it in poll/wait.  Thread-safe. */
+MRI_API int mri_server_submit(mri_server *server, const mri_server_request *request, uint64_t *ticket);
+
+/* *done = 1 once the request has finished (successfully or not). */
+MRI_API int mri_server_poll(mri_server *server, uint64_t ticket, int *done);
+
+/* Wait for a request (timeout_s <= 0: no limit; else MRI_ERR_TIMEOUT after
+ * timeout_s seconds, and the ticket stays valid), copy its image [nx][ny]
+ * to host `image` (nullable) and its submit-to-finish latency in ms to
+ * `latency_ms` (nullable), and retire the ticket.  Returns the request's
+ * own status: MRI_OK, MRI_ERR_NOMEM (does not fit the budget),
+ * MRI_ERR_TIMEOUT (a bounded device-side wait gave up), or the error of
+ * plan creation or launch. */
+MRI_API int mri_server_wait(mri_server *server, uint64_t ticket, mri_c64 *image, double *latency_ms,
+                            double timeout_s);
+
+/* Latency percentiles (ms, nearest-rank) over all requests completed so
+ * far, counts of completed and failed requests, and the device bytes held
+ * now and at most so far by cached plans and in-flight requests. */
+MRI_API int mri_server_stats(mri_server *server, double *p50_ms, double *p99_ms, uint64_t *completed,
+                             uint64_t *failed, size_t *resident_bytes, size_t *peak_resident_bytes);
+
+/* Finish in-flight requests, fail the waiting ones, free everything.  No
+ * other call on the server may be in progress or follow. */
+MRI_API int mri_server_destroy(mri_server *server);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free adjoint (the paper has no counterpart; it is a convenience

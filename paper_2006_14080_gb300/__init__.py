@@ -12,6 +12,8 @@ stream.  The functions mirror the C entry points of ``include/mrirecon.h``:
 * :func:`tv_forward`, :func:`tv_adjoint` -- the finite-difference transform Theta
 * :func:`soft_threshold`   -- Eq. 9
 * :func:`admm_reconstruct` -- Alg. 4
+* :class:`Batch`           -- many reconstructions in one launch
+* :class:`Server`          -- requests from host memory under a device-memory budget
 
 Tensors are CUDA, contiguous, complex64 (images ``[nx, ny]``, coil maps
 ``[nc, nx, ny]``, k-space ``[nc, nk]``) or float32 (trajectory ``[nk, 2]``).
@@ -57,6 +59,12 @@ class Request(ctypes.Structure):
                 ("image_out", ctypes.c_void_p), ("params", AdmmParams)]
 
 
+class ServerRequest(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nk", ctypes.c_int), ("nc", ctypes.c_int),
+                ("traj", ctypes.c_void_p), ("kspace", ctypes.c_void_p), ("coil_maps", ctypes.c_void_p),
+                ("params", AdmmParams)]
+
+
 _lib = None
 
 
@@ -77,6 +85,7 @@ def load(path: str = LIB_PATH):
         "mri_plan_destroy": ([P], I),
         "mri_plan_sync_status": ([P, P], I),
         "mri_plan_device_bytes": ([P], Z),
+        "mri_plan_estimate_bytes": ([I, I, I, I, I], Z),
         "mri_nudft_forward": ([P, P, P, P, P], I),
         "mri_nudft_adjoint": ([P, P, P, P, P], I),
         "mri_normal_op": ([P, P, P, F, P, P], I),
@@ -98,6 +107,13 @@ def load(path: str = LIB_PATH):
         "mri_batch_destroy": ([P], I),
         "mri_batch_reconstruct": ([P, I, ctypes.POINTER(Request), P], I),
         "mri_batch_launch_count": ([P], ctypes.c_longlong),
+        "mri_server_create": ([ctypes.POINTER(P), Z, I, I], I),
+        "mri_server_submit": ([P, ctypes.POINTER(ServerRequest), ctypes.POINTER(ctypes.c_uint64)], I),
+        "mri_server_poll": ([P, ctypes.c_uint64, ctypes.POINTER(I)], I),
+        "mri_server_wait": ([P, ctypes.c_uint64, P, ctypes.POINTER(D), D], I),
+        "mri_server_stats": ([P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(ctypes.c_uint64),
+                              ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Z), ctypes.POINTER(Z)], I),
+        "mri_server_destroy": ([P], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -348,6 +364,90 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None) is not None:
             load().mri_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def estimate_plan_bytes(nx: int, ny: int, nk: int, nc: int, precision: str = "bf16x3") -> int:
+    """Device bytes a plan of this shape would hold (``mri_plan_estimate_bytes``)."""
+    return int(load().mri_plan_estimate_bytes(nx, ny, nk, nc, PRECISIONS[precision]))
+
+
+class Server:
+    """Serving loop (``mri_server_*``): requests from HOST arrays, admitted under
+    a device-memory budget and run concurrently on ``max_inflight`` streams.
+
+    ``submit`` takes numpy arrays (or CPU tensors): ``traj`` float32
+    ``[nk, 2]``, ``kspace`` complex64 ``[nc, nk]``, ``coil_maps`` complex64
+    ``[nc, nx, ny]``; it copies them and returns a ticket.  ``wait(ticket)``
+    returns ``(image, latency_ms)`` with ``image`` a complex64 numpy array
+    ``[nx, ny]``, or raises :class:`MriError` with the request's status.
+    """
+
+    def __init__(self, budget_bytes: int, max_inflight: int = 4, precision: str = "bf16x3"):
+        h = ctypes.c_void_p()
+        _check(load().mri_server_create(ctypes.byref(h), int(budget_bytes), int(max_inflight),
+                                        PRECISIONS[precision]))
+        self._h = h
+        self._shapes = {}
+
+    def submit(self, traj, kspace, coil_maps, lam: float, beta: float, admm_iters: int, cg_iters: int,
+               rtol: float = 0.0, atol: float = 0.0) -> int:
+        import numpy as np
+        traj = np.ascontiguousarray(np.asarray(traj), dtype=np.float32)
+        kspace = np.ascontiguousarray(np.asarray(kspace), dtype=np.complex64)
+        coil_maps = np.ascontiguousarray(np.asarray(coil_maps), dtype=np.complex64)
+        nc, nx, ny = coil_maps.shape
+        nk = traj.shape[0]
+        if traj.shape != (nk, 2) or kspace.shape != (nc, nk):
+            raise ValueError(f"inconsistent shapes: traj {traj.shape}, kspace {kspace.shape}, maps {coil_maps.shape}")
+        req = ServerRequest(nx, ny, nk, nc, traj.ctypes.data, kspace.ctypes.data, coil_maps.ctypes.data,
+                            AdmmParams(float(lam), float(beta), int(admm_iters), int(cg_iters), float(rtol),
+                                       float(atol)))
+        t = ctypes.c_uint64()
+        _check(load().mri_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
+        self._shapes[t.value] = (nx, ny)
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        done = ctypes.c_int()
+        _check(load().mri_server_poll(self._h, ticket, ctypes.byref(done)))
+        return bool(done.value)
+
+    def wait(self, ticket: int, timeout_s: float = 0.0):
+        import numpy as np
+        nx, ny = self._shapes[ticket]
+        img = np.empty((nx, ny), dtype=np.complex64)
+        lat = ctypes.c_double()
+        rc = load().mri_server_wait(self._h, ticket, img.ctypes.data, ctypes.byref(lat), float(timeout_s))
+        if rc != MRI_ERR_TIMEOUT or timeout_s <= 0:
+            self._shapes.pop(ticket, None)
+        _check(rc)
+        return img, lat.value
+
+    def stats(self) -> dict:
+        p50, p99 = ctypes.c_double(), ctypes.c_double()
+        done, failed = ctypes.c_uint64(), ctypes.c_uint64()
+        res, peak = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(load().mri_server_stats(self._h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(done),
+                                       ctypes.byref(failed), ctypes.byref(res), ctypes.byref(peak)))
+        return {"p50_ms": p50.value, "p99_ms": p99.value, "completed": done.value, "failed": failed.value,
+                "resident_bytes": res.value, "peak_resident_bytes": peak.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().mri_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

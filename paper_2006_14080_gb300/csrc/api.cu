@@ -314,6 +314,43 @@ MRI_API int mri_plan_sync_status(mri_plan *p, mri_stream_t stream) {
 
 MRI_API size_t mri_plan_device_bytes(const mri_plan *p) { return p ? p->bytes : 0; }
 
+// Mirrors the allocations of mri_plan_create without allocating.
+MRI_API size_t mri_plan_estimate_bytes(int nx, int ny, int nk, int nc, int precision) {
+    if (nx <= 0 || ny <= 0 || nk <= 0 || nc <= 0) return 0;
+    if (precision != MRI_FP32 && precision != MRI_BF16X3) return 0;
+    mri_plan t;
+    t.nx = nx;
+    t.ny = ny;
+    t.nk = nk;
+    t.nc = nc;
+    t.precision = precision;
+    if (cudaGetDevice(&t.device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, t.device) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    t.nx_pad = round_up(nx, 64);
+    t.ny_pad = round_up(ny, 16);
+    t.kx = round_up(2 * nx, 64);
+    t.kk = round_up(2 * nk, 64);
+    t.nk_pad = round_up(nk, 32);
+    const size_t npix = (size_t)nx * ny, c64 = sizeof(float2), bf = 2;
+    size_t bytes = 0;
+    if (precision == MRI_BF16X3) {
+        if (tc_plan_tiling(&t) != MRI_OK) return 0;
+        bytes += c64 * ((size_t)nx * t.nk_pad + (size_t)ny * t.nk_pad);
+        bytes += bf * (2 * (size_t)2 * nk * t.kx + 2 * (size_t)t.ny_pad * t.kk + 2 * (size_t)nc * t.ny_pad * t.kx);
+    } else {
+        int per = 0;
+        t.ksplit = choose_ksplit_fp32(&t, &per);
+        bytes += c64 * ((size_t)nk * nx + (size_t)nk * ny + (size_t)nc * npix);
+    }
+    bytes += c64 * ((size_t)nc * t.nk_pad + (size_t)t.ksplit * nc * ny * t.nx_pad + 7 * npix + 4 * npix);
+    bytes += sizeof(double) * (size_t)(2 * std::max(1024, ceil_div(nx, 32) * ny));
+    bytes += sizeof(DevScalars);
+    return bytes;
+}
+
 MRI_API int mri_nudft_forward(mri_plan *p, const mri_c64 *image, const mri_c64 *maps, mri_c64 *kspace,
                               mri_stream_t stream) {
     if (!p || !image || !maps || !kspace) return fail(MRI_ERR_INVALID, "null argument");
