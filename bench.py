@@ -35,6 +35,33 @@ METRIC = ("ADMM recon/s, N=128 image, 12 coils, 64 golden-angle spokes x 256 sam
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# product kernels on this workload, from one ncu capture each (the summaries
+# under profiles/ give the command), keyed by a hash of the kernel sources as
+# captured: a changed kernel reports traffic null until it is captured again.
+NCU_TRAFFIC = {
+    "adj_tc_kernel": (37.34e6, "7709b8a2e9c4c531", "profiles/adj_tc_kernel_n128.md"),
+    "fwd_tc_kernel": (53.10e6, "7709b8a2e9c4c531", "profiles/fwd_tc_kernel_n128.md"),
+}
+TC_SOURCES = ("nudft_tc.cu", "tc_ptx.cuh", "internal.h", "common.cuh")
+
+
+def tc_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in TC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2006_14080_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(kernel: str):
+    entry = NCU_TRAFFIC.get(kernel)
+    if entry is None or entry[1] != tc_source_hash():
+        return None, None
+    return entry[0], entry[2]
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -249,6 +276,8 @@ def run_gpu(args, rank, world, local_rank):
     achieved = executed / (dom_avg_ms * 1e-3) / 1e12
     peak_tf = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
     useful_tflops_step = normal_ops_per_recon(p) * 2 * flops_prod / (total_ms / args.steps * 1e-3) / 1e12
+    dom_kernel = "adj_tc_kernel" if dom == "adj" else "fwd_tc_kernel"
+    traffic, traffic_src = captured_traffic(dom_kernel)
     nrmse_vs_golden = None
     gpath = os.path.join(ROOT, "tests", "golden", f"admm_{p.name}.npz")
     if os.path.exists(gpath):
@@ -277,9 +306,9 @@ def run_gpu(args, rank, world, local_rank):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "tuning": tuned,
-        "roofline": {"bound": "tensor", "kernel": "adj_tc_kernel" if dom == "adj" else "fwd_tc_kernel",
+        "roofline": {"bound": "tensor", "kernel": dom_kernel,
                      "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf,
-                     "traffic": None,
+                     "traffic": traffic, "traffic_unit": "bytes per launch", "traffic_source": traffic_src,
                      "note": f"executed bf16 tensor flops (3 products x 8*nk*nx*ny*nc) per launch / mean launch "
                              f"time ({dom_avg_ms:.4f} ms over {timing[dom + '_launches']} launches, CUDA events on "
                              f"the launching stream in a directly-launched pass of the same steps), "
