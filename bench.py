@@ -4,9 +4,12 @@ One step = one complete reconstruction of the N=128 workload (12 coils, 64
 golden-angle spokes x 256 readout samples, 30 ADMM x 8 CG iterations,
 lambda=1e-3, beta=1): DFT-factor generation for the step's trajectory
 (Alg. 1) followed by Alg. 4 with Alg. 2 inside, in the BF16x3 tensor-core
-form.  The plain FP32 form is timed beside it on the same GPU.
+form.  The TF32 tensor-core form and the plain FP32 form are timed beside it
+on the same GPU.  Other workloads: --workload n256 (N=256, 32 coils, 128 x
+512 samples, 50 x 10 iterations), batch64 (64 heterogeneous reconstructions
+in one launch), serve (the serving loop under Poisson arrivals).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload W]
 
 Prints one JSON line.  Each rank reconstructs its own problems (independent
 reconstructions: weak scaling, no collective on the data path).
@@ -29,9 +32,8 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-WORKLOAD = "n128_c12_s64x256_admm30x8"
-METRIC = ("ADMM recon/s, N=128 image, 12 coils, 64 golden-angle spokes x 256 samples, 30 ADMM x 8 CG, "
-          "BF16x3 tensor-core NUDFT (FP32 form beside)")
+# single-reconstruction workloads: N=128 (the headline) and N=256
+WORKLOADS = {"n128": synth.config_medium, "n256": synth.config_large}
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
@@ -40,8 +42,8 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # under profiles/ give the command), keyed by a hash of the kernel sources as
 # captured: a changed kernel reports traffic null until it is captured again.
 NCU_TRAFFIC = {
-    "adj_tc_kernel": (37.34e6, "7709b8a2e9c4c531", "profiles/adj_tc_kernel_n128.md"),
-    "fwd_tc_kernel": (53.10e6, "7709b8a2e9c4c531", "profiles/fwd_tc_kernel_n128.md"),
+    ("adj_tc_kernel", "n128_c12_s64x256"): (37.34e6, "7709b8a2e9c4c531", "profiles/adj_tc_kernel_n128.md"),
+    ("fwd_tc_kernel", "n128_c12_s64x256"): (53.10e6, "7709b8a2e9c4c531", "profiles/fwd_tc_kernel_n128.md"),
 }
 TC_SOURCES = ("nudft_tc.cu", "tc_ptx.cuh", "internal.h", "common.cuh")
 
@@ -55,8 +57,8 @@ def tc_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def captured_traffic(kernel: str):
-    entry = NCU_TRAFFIC.get(kernel)
+def captured_traffic(kernel: str, workload: str):
+    entry = NCU_TRAFFIC.get((kernel, workload))
     if entry is None or entry[1] != tc_source_hash():
         return None, None
     return entry[0], entry[2]
@@ -71,8 +73,17 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def problem():
-    return synth.config_medium()
+def problem(workload: str = "n128"):
+    return WORKLOADS[workload]()
+
+
+def workload_name(p) -> str:
+    return f"{p.name}_admm{p.admm_iters}x{p.cg_iters}"
+
+
+def metric_name(p) -> str:
+    return (f"ADMM recon/s, N={p.nx} image, {p.nc} coils, {p.spokes} golden-angle spokes x {p.readout} samples, "
+            f"{p.admm_iters} ADMM x {p.cg_iters} CG, BF16x3 tensor-core NUDFT (TF32 and FP32 forms beside)")
 
 
 def normal_ops_per_recon(p):
@@ -149,7 +160,7 @@ def run_gpu(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    p = problem()
+    p = problem(args.workload)
     # a created (non-legacy) stream: the library captures each reconstruction
     # into a CUDA graph on first use and replays it on such streams
     torch.cuda.set_stream(torch.cuda.Stream(device=dev))
@@ -257,6 +268,17 @@ def run_gpu(args, rank, world, local_rank):
             timing32 = plan32.read_timing()
             x_fp32 = out.cpu().numpy()
 
+    tf32 = None
+    if "tf32" in forms:
+        with mr.Plan(p.nx, p.ny, p.nc, traj, "tf32") as plan_t:
+            tuned_t = plan_t.autotune(repeats=5)
+            tt, lt_ = timed_steps(plan_t, out, args.steps, args.warmup)
+            x_tf32 = out.cpu().numpy()
+            plan_t.set_timing(True)
+            timed_steps(plan_t, out, max(2, args.steps // 4), 1, plan_timed=True)
+            timing_t = plan_t.read_timing()
+        tf32 = (tt, lt_, timing_t, tuned_t, x_tf32)
+
     # ---------------------------------------------------------------- report
     times, launches, timing, clocks = results["bf16x3"]
     total_ms = max_over_ranks(sum(times))
@@ -277,7 +299,7 @@ def run_gpu(args, rank, world, local_rank):
     peak_tf = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
     useful_tflops_step = normal_ops_per_recon(p) * 2 * flops_prod / (total_ms / args.steps * 1e-3) / 1e12
     dom_kernel = "adj_tc_kernel" if dom == "adj" else "fwd_tc_kernel"
-    traffic, traffic_src = captured_traffic(dom_kernel)
+    traffic, traffic_src = captured_traffic(dom_kernel, p.name)
     nrmse_vs_golden = None
     gpath = os.path.join(ROOT, "tests", "golden", f"admm_{p.name}.npz")
     if os.path.exists(gpath):
@@ -286,7 +308,7 @@ def run_gpu(args, rank, world, local_rank):
         if x_fp32 is not None:
             nrmse_vs_golden["fp32"] = float(np.linalg.norm(x_fp32 - xg) / np.linalg.norm(xg))
     line = {
-        "metric": METRIC,
+        "metric": metric_name(p),
         "value": recon_s,
         "unit": "recon/s",
         "n_gpus": world,
@@ -298,7 +320,7 @@ def run_gpu(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "bf16x3/f32",
         "data": "synthetic (seeded ellipse phantom, Gaussian coil maps, golden-angle radial, 0.5% noise)",
-        "config": {"workload": WORKLOAD, "nx": p.nx, "ny": p.ny, "coils": p.nc, "spokes": p.spokes,
+        "config": {"workload": workload_name(p), "nx": p.nx, "ny": p.ny, "coils": p.nc, "spokes": p.spokes,
                    "readout": p.readout, "admm_iters": p.admm_iters, "cg_iters": p.cg_iters, "lambda": p.lam,
                    "beta": p.beta, "l2": "flushed (512 MB write) between timed steps",
                    "step": "factor generation for the step's trajectory + full ADMM reconstruction"},
@@ -325,9 +347,29 @@ def run_gpu(args, rank, world, local_rank):
                       "ms_per_step": t32_ms / fp32_steps, "gpu_launches": l32,
                       "fwd_ms_per_launch": timing32["fwd_ms"] / max(1, timing32["fwd_launches"]),
                       "adj_ms_per_launch": timing32["adj_ms"] / max(1, timing32["adj_launches"])},
+        "tf32_form": None,
         "nrmse_vs_fp64_oracle": nrmse_vs_golden,
         "clocks": clocks,
     }
+    if tf32 is not None:
+        tt, lt_, timing_t, tuned_t, x_tf32 = tf32
+        tt_ms = max_over_ranks(sum(tt))
+        f_avg = timing_t["fwd_ms"] / max(1, timing_t["fwd_launches"])
+        a_avg = timing_t["adj_ms"] / max(1, timing_t["adj_launches"])
+        # one TF32 product executes the useful flops once; TF32 dense peak =
+        # measured BF16 peak x the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
+        tf32_peak = peak_tf * 1.1 / 2.25
+        line["tf32_form"] = {
+            "value": world * args.steps / (tt_ms / 1e3), "unit": "recon/s", "ms_per_step": tt_ms / args.steps,
+            "gpu_launches": lt_, "tuning": tuned_t, "fwd_ms_per_launch": f_avg, "adj_ms_per_launch": a_avg,
+            "fwd_tflops": flops_prod / (f_avg * 1e-3) / 1e12, "adj_tflops": flops_prod / (a_avg * 1e-3) / 1e12,
+            "peak_tflops": tf32_peak, "peak_note": f"{pk_kind} sustained bf16 x 1.1/2.25 (nominal TF32/BF16)",
+            "adj_frac": flops_prod / (a_avg * 1e-3) / 1e12 / tf32_peak,
+            "fwd_frac": flops_prod / (f_avg * 1e-3) / 1e12 / tf32_peak,
+        }
+        if nrmse_vs_golden is not None:
+            xg = np.load(gpath)["x"]
+            nrmse_vs_golden["tf32"] = float(np.linalg.norm(x_tf32 - xg) / np.linalg.norm(xg))
     if "fp32" not in forms:
         line["fp32_form"] = None
     if "e2e" not in forms:
@@ -489,51 +531,68 @@ def run_serve(args, rank, world, local_rank):
     }
 
 
+# complex MACs above which one oracle normal operator takes too long to time
+# whole (N=256: 1.4e11, about 45 s on 16 cores): the sample is then the
+# forward operator on a slice of the k-space samples, scaled to a normal operator
+ORACLE_WHOLE_OP_MACS = 2e10
+
+
 def oracle_sample(p, budget_s):
-    """Time the FP64 oracle's normal operator (Eq. 11) at the workload's full
-    size; one reconstruction needs normal_ops_per_recon() of them."""
+    """Time the FP64 oracle's normal operator (Eq. 11) at the workload's size;
+    one reconstruction needs normal_ops_per_recon() of them.  Returns
+    (seconds per normal operator, timed calls, threads, description)."""
     import oracle
     rng = np.random.default_rng(7)
     x = synth.random_complex(rng, (p.nx, p.ny)).astype(np.complex128)
-    oracle.normal(p.traj, p.maps, p.beta, x)  # warm (threads, pages)
+    macs = float(p.nk) * p.nx * p.ny * p.nc
+    if macs <= ORACLE_WHOLE_OP_MACS:
+        call, scale = (lambda: oracle.normal(p.traj, p.maps, p.beta, x)), 1.0
+        what = "FP64 normal operators (Eq. 11) at full size"
+    else:
+        m = max(1, int(p.nk * ORACLE_WHOLE_OP_MACS / 4 / macs))
+        sub = np.ascontiguousarray(p.traj[:m])
+        call, scale = (lambda: oracle.forward(sub, x, p.maps)), 2.0 * p.nk / m
+        what = (f"FP64 forward operators on the first {m} of {p.nk} k-space samples at full image and coil "
+                f"size, scaled by {scale:.1f} to one normal operator (forward + adjoint over all samples)")
+    call()  # warm (threads, pages)
     times = []
     t_start = time.time()
     while not times or (time.time() - t_start < budget_s and len(times) < 8):
         t0 = time.perf_counter()
-        oracle.normal(p.traj, p.maps, p.beta, x)
+        call()
         times.append(time.perf_counter() - t0)
-    per_op = statistics.median(times)
-    return per_op, len(times), oracle.get_threads()
+    per_op = statistics.median(times) * scale
+    return per_op, len(times), oracle.get_threads(), what
 
 
 def cpu_baseline(p, budget_s):
-    per_op, n, threads = oracle_sample(p, budget_s)
+    per_op, n, threads, what = oracle_sample(p, budget_s)
     return {"value": 1.0 / (per_op * normal_ops_per_recon(p)), "unit": "recon/s", "cores": threads,
             "kind": "oracle",
-            "sample": f"{n} FP64 normal operators (Eq. 11) at the full {WORKLOAD} size, median "
-                      f"{per_op:.2f} s each, scaled by {normal_ops_per_recon(p)} operators per reconstruction"}
+            "sample": f"{n} timed calls: {what} ({workload_name(p)}), {per_op:.2f} s per normal operator, "
+                      f"scaled by {normal_ops_per_recon(p)} operators per reconstruction"}
 
 
 def run_reference(args, rank):
     if rank != 0:
         return None
-    p = problem()
+    p = problem(args.workload if args.workload in WORKLOADS else "n128")
     per_step = []
     for _ in range(args.warmup):
         oracle_sample(p, 0.0)
     for _ in range(args.steps):
-        per_op, _, threads = oracle_sample(p, 0.0)
+        per_op, _, threads, what = oracle_sample(p, 0.0)
         per_step.append(per_op * normal_ops_per_recon(p))
     total = sum(per_step)
     value = args.steps / total
     return {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "recon/s", "n_gpus": 1,
+        "impl": "reference", "metric": metric_name(p), "value": value, "unit": "recon/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "data": "synthetic", "config": {"workload": workload_name(p)},
         "cpu_baseline": {"value": value, "unit": "recon/s", "cores": threads, "kind": "oracle",
-                         "sample": "each step: one FP64 normal operator (Eq. 11) at full size, scaled by "
-                                   f"{normal_ops_per_recon(p)} operators per reconstruction"},
+                         "sample": f"each step: {what}, scaled by {normal_ops_per_recon(p)} operators per "
+                                   "reconstruction"},
         "e2e": {"value": value, "unit": "recon/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -546,19 +605,23 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--workload", default="n128", choices=["n128", "batch64", "serve"],
-                    help="n128: the single N=128 reconstruction (default); batch64: 64 heterogeneous "
-                         "reconstructions in one batched launch; serve: the serving loop under Poisson arrivals")
+    ap.add_argument("--workload", default="n128", choices=["n128", "n256", "batch64", "serve"],
+                    help="n128: the single N=128 reconstruction (default); n256: the N=256, 32-coil "
+                         "reconstruction; batch64: 64 heterogeneous reconstructions in one batched launch; "
+                         "serve: the serving loop under Poisson arrivals")
     ap.add_argument("--batch-items", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-inflight", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=32.0)
     ap.add_argument("--clusters", default="",
                     help="'F,A': forward and adjoint cluster sizes instead of autotuning them")
-    ap.add_argument("--forms", default="bf16x3,e2e,fp32",
+    ap.add_argument("--forms", default="",
                     help="comma list of what to run: bf16x3 (always), e2e (host-buffer run), fp32 (plain FP32 "
-                         "form); the default runs all three")
+                         "form), tf32 (TF32 tensor-core form); default all four for n128, all but fp32 for "
+                         "n256 (whose FP32 form takes about half a minute per reconstruction)")
     args = ap.parse_args()
+    if not args.forms:
+        args.forms = "bf16x3,e2e,tf32" if args.workload == "n256" else "bf16x3,e2e,fp32,tf32"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

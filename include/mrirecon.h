@@ -66,6 +66,8 @@ typedef struct mri_plan mri_plan;
 
 /* Arithmetic of the two dense products inside the DFT operators. */
 #define MRI_FP32   0  /* FP32 FFMA on the CUDA cores */
+#define MRI_TF32   1  /* tcgen05 TF32 tensor cores: operands rounded to TF32
+                         (10-bit mantissa, nearest), one product, FP32 accumulation */
 #define MRI_BF16X3 2  /* tcgen05 BF16 tensor cores, hi+lo split operands, three
                          products (hi*hi + hi*lo + lo*hi), FP32 accumulation */
 
@@ -81,7 +83,7 @@ MRI_API int mri_version(void);
  * per-core operator generation of Alg. 1, in separable form.  The phase
  * k*x is formed and reduced to [-1/2, 1/2] in FP64 before the FP32 sine and
  * cosine.  traj is read during the call (stream-ordered on `stream`) and not
- * kept.  precision is MRI_FP32 or MRI_BF16X3.  Allocates device memory (the
+ * kept.  precision is MRI_FP32, MRI_TF32 or MRI_BF16X3.  Allocates device memory (the
  * factors plus workspace, O(nk*(nx+ny)) + O(nc*nx*ny)); *plan receives the
  * handle, or NULL on error.
  */
@@ -249,8 +251,8 @@ typedef struct {
     mri_admm_params params;
 } mri_server_request;
 
-/* Start a server on the current device.  precision: MRI_FP32 or
- * MRI_BF16X3 for all its plans; max_inflight in 1..64. */
+/* Start a server on the current device.  precision: MRI_FP32, MRI_TF32
+ * or MRI_BF16X3 for all its plans; max_inflight in 1..64. */
 MRI_API int mri_server_create(mri_server **server, size_t hbm_budget_bytes, int max_inflight, int precision);
 
 /* Queue a request; *ticket identifies it in poll/wait.  Thread-safe. */
@@ -320,6 +322,14 @@ MRI_API int mri_plan_read_timing(mri_plan *plan, double *fwd_ms, long long *fwd_
 
 /* Number of kernels this plan has enqueued since creation. */
 MRI_API long long mri_plan_launch_count(const mri_plan *plan);
+
+/* Self-test of failure detection: enqueue one thread that waits on a
+ * device barrier nothing completes, through the same bounded wait the
+ * tensor-core kernels use; after limit_ms (0 < limit_ms <= 1000) it gives up
+ * and records the timeout in the plan's deferred status, so that the next
+ * mri_plan_sync_status returns MRI_ERR_TIMEOUT (and clears it).  The device
+ * context stays usable. */
+MRI_API int mri_plan_selftest_wait(mri_plan *plan, double limit_ms, mri_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Scheduling of the tensor-core products (not in the paper).  The forward

@@ -39,8 +39,9 @@ MRI_ERR_TIMEOUT = -4
 MRI_ERR_UNSUPPORTED = -5
 
 MRI_FP32 = 0
+MRI_TF32 = 1
 MRI_BF16X3 = 2
-PRECISIONS = {"fp32": MRI_FP32, "bf16x3": MRI_BF16X3}
+PRECISIONS = {"fp32": MRI_FP32, "tf32": MRI_TF32, "bf16x3": MRI_BF16X3}
 
 
 class MriError(RuntimeError):
@@ -99,6 +100,7 @@ def load(path: str = LIB_PATH):
                                   ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
                                   ctypes.POINTER(ctypes.c_longlong)], I),
         "mri_plan_launch_count": ([P], ctypes.c_longlong),
+        "mri_plan_selftest_wait": ([P, D, P], I),
         "mri_plan_get_config": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "mri_plan_set_clusters": ([P, I, I], I),
         "mri_plan_autotune": ([P, I, P], I),
@@ -194,6 +196,10 @@ class Plan:
 
     def launch_count(self) -> int:
         return int(load().mri_plan_launch_count(self.handle))
+
+    def selftest_wait(self, limit_ms: float, stream=None):
+        """Enqueue a bounded wait that runs out after ``limit_ms`` (failure-detection self-test)."""
+        _check(load().mri_plan_selftest_wait(self.handle, float(limit_ms), _stream(stream)))
 
     def config(self) -> dict:
         v = [ctypes.c_int() for _ in range(4)]

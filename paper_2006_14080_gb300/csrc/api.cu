@@ -61,9 +61,10 @@ int dev_alloc(mri_plan *p, T **ptr, size_t count) {
 void free_plan(mri_plan *p) {
     if (!p) return;
     invalidate_graph(p);
-    void *bufs[] = {p->ax,  p->ay,  p->axT,  p->ayT,   p->afwd_hi, p->afwd_lo, p->badj_hi, p->badj_lo,
-                    p->bfwd_hi, p->bfwd_lo, p->bsx, p->y, p->part, p->x, p->xprev, p->r,
-                    p->d,   p->ad,  p->b,    p->fhd,   p->mu,      p->eta,     p->partials, p->scal};
+    void *bufs[] = {p->ax,      p->ay,      p->axT,     p->ayT,    p->afwd_hi, p->afwd_lo, p->badj_hi,
+                    p->badj_lo, p->bfwd_hi, p->bfwd_lo, p->afwd_t, p->badj_t,  p->bfwd_t,  p->bsx,
+                    p->y,       p->part,    p->x,       p->xprev,  p->r,       p->d,       p->ad,
+                    p->b,       p->fhd,     p->mu,      p->eta,    p->partials, p->scal};
     for (void *q : bufs)
         if (q) cudaFree(q);
     for (cudaEvent_t e : p->ev_free) cudaEventDestroy(e);
@@ -83,6 +84,9 @@ int choose_ksplit_fp32(const mri_plan *p, int *samples_per_split) {
     const int tiles = ceil_div(p->nx, 64) * ceil_div(p->ny, 64) * p->nc;
     const int target = 2 * p->num_sms;
     int split = std::max(1, std::min(ceil_div(target, tiles), ceil_div(p->nk, 256)));
+    // at most 4096 samples summed in one FP32 run: rounding error of a
+    // sequential FP32 sum of L random-phase terms grows like 2^-24 sqrt(L)
+    split = std::max(split, ceil_div(p->nk, 4096));
     split = std::min(split, 64);
     int per = round_up(ceil_div(p->nk, split), 16);
     split = ceil_div(p->nk, per);
@@ -125,8 +129,8 @@ static void timing_disarm(mri_plan *p, std::vector<std::pair<cudaEvent_t, cudaEv
 static cudaError_t op_forward(mri_plan *p, const float2 *image, const float2 *maps, float2 *out, int ld, int skip,
                               cudaStream_t s) {
     const bool timed = timing_arm(p);
-    cudaError_t e = p->precision == MRI_BF16X3 ? launch_fwd_tc(p, image, maps, out, ld, skip, s)
-                                               : launch_fwd_fp32(p, image, maps, out, ld, skip, s);
+    cudaError_t e = is_tc_precision(p->precision) ? launch_fwd_tc(p, image, maps, out, ld, skip, s)
+                                                  : launch_fwd_fp32(p, image, maps, out, ld, skip, s);
     if (timed) timing_disarm(p, p->ev_fwd);
     return e;
 }
@@ -141,7 +145,7 @@ static cudaError_t op_adjoint_partials(mri_plan *p, const float2 *kspace, int sk
         if (e != cudaSuccess) return e;
     }
     const bool timed = timing_arm(p);
-    cudaError_t e = p->precision == MRI_BF16X3 ? launch_adj_tc(p, skip, s) : launch_adj_fp32(p, skip, s);
+    cudaError_t e = is_tc_precision(p->precision) ? launch_adj_tc(p, skip, s) : launch_adj_fp32(p, skip, s);
     if (timed) timing_disarm(p, p->ev_adj);
     return e;
 }
@@ -187,7 +191,7 @@ MRI_API int mri_plan_create(mri_plan **out, int nx, int ny, int nk, int nc, cons
     if ((long long)nx * ny > (1LL << 26) || nk > (1 << 28) || nc > 4096)
         return fail(MRI_ERR_INVALID, "dimensions too large");
     if (!traj) return fail(MRI_ERR_INVALID, "trajectory pointer is null");
-    if (precision != MRI_FP32 && precision != MRI_BF16X3) return fail(MRI_ERR_INVALID, "unknown precision");
+    if (precision != MRI_FP32 && !is_tc_precision(precision)) return fail(MRI_ERR_INVALID, "unknown precision");
     cudaStream_t s = (cudaStream_t)stream;
 
     mri_plan *p = new mri_plan();
@@ -212,25 +216,32 @@ MRI_API int mri_plan_create(mri_plan **out, int nx, int ny, int nk, int nc, cons
 
     int rc = MRI_OK;
     const size_t npix = (size_t)nx * ny;
-    if (precision == MRI_BF16X3) {
+    if (is_tc_precision(precision)) {
+        const std::string form = precision == MRI_TF32 ? "TF32" : "BF16x3";
         std::string why;
         if (!tc_supported(p, &why)) {
             delete p;
-            return fail(MRI_ERR_UNSUPPORTED, "BF16x3 tensor-core path: " + why);
+            return fail(MRI_ERR_UNSUPPORTED, form + " tensor-core path: " + why);
         }
         rc = tc_plan_tiling(p);
         if (rc != MRI_OK) {
             delete p;
-            return fail(rc, "BF16x3 tensor-core path: shared-memory plan does not fit");
+            return fail(rc, form + " tensor-core path: shared-memory plan does not fit");
         }
         if (rc == MRI_OK) rc = dev_alloc(p, &p->axT, (size_t)nx * p->nk_pad);
         if (rc == MRI_OK) rc = dev_alloc(p, &p->ayT, (size_t)ny * p->nk_pad);
-        if (rc == MRI_OK) rc = dev_alloc(p, &p->afwd_hi, (size_t)2 * nk * p->kx);
-        if (rc == MRI_OK) rc = dev_alloc(p, &p->afwd_lo, (size_t)2 * nk * p->kx);
-        if (rc == MRI_OK) rc = dev_alloc(p, &p->badj_hi, (size_t)p->ny_pad * p->kk);
-        if (rc == MRI_OK) rc = dev_alloc(p, &p->badj_lo, (size_t)p->ny_pad * p->kk);
-        if (rc == MRI_OK) rc = dev_alloc(p, &p->bfwd_hi, (size_t)nc * p->ny_pad * p->kx);
-        if (rc == MRI_OK) rc = dev_alloc(p, &p->bfwd_lo, (size_t)nc * p->ny_pad * p->kx);
+        if (precision == MRI_TF32) {
+            if (rc == MRI_OK) rc = dev_alloc(p, &p->afwd_t, (size_t)2 * nk * p->kx);
+            if (rc == MRI_OK) rc = dev_alloc(p, &p->badj_t, (size_t)p->ny_pad * p->kk);
+            if (rc == MRI_OK) rc = dev_alloc(p, &p->bfwd_t, (size_t)nc * p->ny_pad * p->kx);
+        } else {
+            if (rc == MRI_OK) rc = dev_alloc(p, &p->afwd_hi, (size_t)2 * nk * p->kx);
+            if (rc == MRI_OK) rc = dev_alloc(p, &p->afwd_lo, (size_t)2 * nk * p->kx);
+            if (rc == MRI_OK) rc = dev_alloc(p, &p->badj_hi, (size_t)p->ny_pad * p->kk);
+            if (rc == MRI_OK) rc = dev_alloc(p, &p->badj_lo, (size_t)p->ny_pad * p->kk);
+            if (rc == MRI_OK) rc = dev_alloc(p, &p->bfwd_hi, (size_t)nc * p->ny_pad * p->kx);
+            if (rc == MRI_OK) rc = dev_alloc(p, &p->bfwd_lo, (size_t)nc * p->ny_pad * p->kx);
+        }
     } else {
         int per = 0;
         p->ksplit = choose_ksplit_fp32(p, &per);
@@ -262,13 +273,17 @@ MRI_API int mri_plan_create(mri_plan **out, int nx, int ny, int nk, int nc, cons
         size_t zn[] = {(size_t)2 * nk * p->kx, (size_t)2 * nk * p->kx, (size_t)p->ny_pad * p->kk,
                        (size_t)p->ny_pad * p->kk, (size_t)nc * p->ny_pad * p->kx, (size_t)nc * p->ny_pad * p->kx};
         for (int q = 0; q < 6 && e == cudaSuccess; ++q) e = cudaMemsetAsync(zb[q], 0, zn[q] * 2, s);
+    } else if (precision == MRI_TF32) {
+        float *zt[] = {p->afwd_t, p->badj_t, p->bfwd_t};
+        size_t zn[] = {(size_t)2 * nk * p->kx, (size_t)p->ny_pad * p->kk, (size_t)nc * p->ny_pad * p->kx};
+        for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaMemsetAsync(zt[q], 0, zn[q] * 4, s);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(p->part, 0, (size_t)p->ksplit * nc * ny * p->nx_pad * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->y, 0, (size_t)nc * p->nk_pad * 8, s);
     if (e == cudaSuccess && p->axT) e = cudaMemsetAsync(p->axT, 0, (size_t)nx * p->nk_pad * 8, s);
     if (e == cudaSuccess && p->ayT) e = cudaMemsetAsync(p->ayT, 0, (size_t)ny * p->nk_pad * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->scal, 0, sizeof(DevScalars), s);
-    if (e == cudaSuccess && precision == MRI_BF16X3) {
+    if (e == cudaSuccess && is_tc_precision(precision)) {
         rc = tc_make_tensor_maps(p);
         if (rc != MRI_OK) {
             free_plan(p);
@@ -317,7 +332,7 @@ MRI_API size_t mri_plan_device_bytes(const mri_plan *p) { return p ? p->bytes : 
 // Mirrors the allocations of mri_plan_create without allocating.
 MRI_API size_t mri_plan_estimate_bytes(int nx, int ny, int nk, int nc, int precision) {
     if (nx <= 0 || ny <= 0 || nk <= 0 || nc <= 0) return 0;
-    if (precision != MRI_FP32 && precision != MRI_BF16X3) return 0;
+    if (precision != MRI_FP32 && !is_tc_precision(precision)) return 0;
     mri_plan t;
     t.nx = nx;
     t.ny = ny;
@@ -336,7 +351,8 @@ MRI_API size_t mri_plan_estimate_bytes(int nx, int ny, int nk, int nc, int preci
     t.nk_pad = round_up(nk, 32);
     const size_t npix = (size_t)nx * ny, c64 = sizeof(float2), bf = 2;
     size_t bytes = 0;
-    if (precision == MRI_BF16X3) {
+    if (is_tc_precision(precision)) {
+        // BF16x3 hi + lo (2 + 2 bytes) and TF32 (4 bytes) operands take the same bytes
         if (tc_plan_tiling(&t) != MRI_OK) return 0;
         bytes += c64 * ((size_t)nx * t.nk_pad + (size_t)ny * t.nk_pad);
         bytes += bf * (2 * (size_t)2 * nk * t.kx + 2 * (size_t)t.ny_pad * t.kk + 2 * (size_t)nc * t.ny_pad * t.kx);
@@ -566,7 +582,8 @@ MRI_API int mri_plan_get_config(const mri_plan *p, int *fwd_cluster, int *adj_cl
 
 MRI_API int mri_plan_set_clusters(mri_plan *p, int fwd_cluster, int adj_cluster) {
     if (!p) return fail(MRI_ERR_INVALID, "null plan");
-    if (p->precision != MRI_BF16X3) return fail(MRI_ERR_UNSUPPORTED, "cluster sizes apply to the tensor-core form");
+    if (!is_tc_precision(p->precision))
+        return fail(MRI_ERR_UNSUPPORTED, "cluster sizes apply to the tensor-core forms");
     return tc_set_clusters(p, fwd_cluster, adj_cluster);
 }
 
@@ -577,7 +594,7 @@ MRI_API int mri_plan_set_clusters(mri_plan *p, int fwd_cluster, int adj_cluster)
 // synchronises the stream.
 MRI_API int mri_plan_autotune(mri_plan *p, int repeats, mri_stream_t stream) {
     if (!p) return fail(MRI_ERR_INVALID, "null plan");
-    if (p->precision != MRI_BF16X3) return MRI_OK;  // the FP32 form has nothing to tune
+    if (!is_tc_precision(p->precision)) return MRI_OK;  // the FP32 form has nothing to tune
     if (repeats <= 0) repeats = 3;
     cudaStream_t s = (cudaStream_t)stream;
     float2 *maps = nullptr;

@@ -4,10 +4,11 @@
 // (exact: a 24-bit mantissa times a small integer) and reduced to [-1/2, 1/2]
 // by subtracting the nearest integer, also exact; only then is it rounded to
 // FP32 for sincospif.  Besides the FP32 factors, the kernel writes the
-// tensor-core operands: BF16 hi/lo splits of the real embedding of A_x
-// (forward product) and of conj(A_y) (adjoint product).
+// tensor-core operands: the real embedding of A_x (forward product) and of
+// conj(A_y) (adjoint product), as BF16 hi/lo splits or as TF32-rounded FP32.
 #include "common.cuh"
 #include "internal.h"
+#include "tc_ptx.cuh"
 
 namespace mri {
 
@@ -34,17 +35,21 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t &hi, uint3
     lo = pack_bf16(al, bl);
 }
 
+// TF32-rounded pair (a, b) as one 64-bit word (a first).
+__device__ __forceinline__ uint2 tf32_pair(float a, float b) { return make_uint2(tc::tf32_bits(a), tc::tf32_bits(b)); }
+
 // One 32 (samples) x 32 (pixel index) tile of one axis.  block = (32, 8).
 // F [nk][n] and FT [n][nk] are the FP32 factor and its transpose (either may
 // be null).  emb_hi/lo (nullable) receive the forward-product embedding
 // rows 2k: (Re, -Im), 2k+1: (Im, Re) at columns 2*idx, leading dim ld_emb.
 // cemb_hi/lo (nullable) receive the adjoint-product embedding of conj(F):
-// row idx, columns 2k, 2k+1 = (Re, -Im), leading dim ld_cemb.
+// row idx, columns 2k, 2k+1 = (Re, -Im), leading dim ld_cemb.  emb_t and
+// cemb_t (nullable) receive the same embeddings as TF32-rounded FP32.
 __global__ void factor_tile_kernel(const float *__restrict__ traj, int axis, int n, int nk,
                                    float2 *__restrict__ F, float2 *__restrict__ FT, int ld_t,
-                                   uint32_t *__restrict__ emb_hi, uint32_t *__restrict__ emb_lo, int ld_emb,
-                                   uint32_t *__restrict__ cemb_hi, uint32_t *__restrict__ cemb_lo,
-                                   int ld_cemb) {
+                                   uint32_t *__restrict__ emb_hi, uint32_t *__restrict__ emb_lo,
+                                   uint2 *__restrict__ emb_t, int ld_emb, uint32_t *__restrict__ cemb_hi,
+                                   uint32_t *__restrict__ cemb_lo, uint2 *__restrict__ cemb_t, int ld_cemb) {
     __shared__ float2 tile[32][33];
     const int k0 = blockIdx.x * 32, p0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -66,6 +71,10 @@ __global__ void factor_tile_kernel(const float *__restrict__ traj, int axis, int
                 emb_hi[((size_t)(2 * k + 1) * ld_emb) / 2 + idx] = h;
                 emb_lo[((size_t)(2 * k + 1) * ld_emb) / 2 + idx] = l;
             }
+            if (emb_t) {
+                emb_t[((size_t)(2 * k) * ld_emb) / 2 + idx] = tf32_pair(v.x, -v.y);
+                emb_t[((size_t)(2 * k + 1) * ld_emb) / 2 + idx] = tf32_pair(v.y, v.x);
+            }
         }
         tile[q][tx] = v;
     }
@@ -83,6 +92,7 @@ __global__ void factor_tile_kernel(const float *__restrict__ traj, int axis, int
                 cemb_hi[((size_t)idx * ld_cemb) / 2 + k] = h;
                 cemb_lo[((size_t)idx * ld_cemb) / 2 + k] = l;
             }
+            if (cemb_t) cemb_t[((size_t)idx * ld_cemb) / 2 + k] = tf32_pair(v.x, -v.y);
         }
     }
 }
@@ -94,14 +104,14 @@ cudaError_t launch_factors(mri_plan *p, const float *traj, cudaStream_t s) {
     {
         dim3 grid(ceil_div(p->nk, 32), ceil_div(p->nx, 32));
         factor_tile_kernel<<<grid, block, 0, s>>>(traj, 0, p->nx, p->nk, p->ax, p->axT, p->nk_pad,
-                                                  (uint32_t *)p->afwd_hi, (uint32_t *)p->afwd_lo, p->kx,
-                                                  nullptr, nullptr, 0);
+                                                  (uint32_t *)p->afwd_hi, (uint32_t *)p->afwd_lo,
+                                                  (uint2 *)p->afwd_t, p->kx, nullptr, nullptr, nullptr, 0);
     }
     {
         dim3 grid(ceil_div(p->nk, 32), ceil_div(p->ny, 32));
         factor_tile_kernel<<<grid, block, 0, s>>>(traj, 1, p->ny, p->nk, p->ay, p->ayT, p->nk_pad, nullptr,
-                                                  nullptr, 0, (uint32_t *)p->badj_hi, (uint32_t *)p->badj_lo,
-                                                  p->kk);
+                                                  nullptr, nullptr, 0, (uint32_t *)p->badj_hi,
+                                                  (uint32_t *)p->badj_lo, (uint2 *)p->badj_t, p->kk);
     }
     return cudaGetLastError();
 }

@@ -48,6 +48,8 @@ enum Counter : int { kCntDot = 0, kCntTau = 1, kCntInit = 2, kCntDual = 3, kCntO
 constexpr int kTcBlockM = 128;   // UMMA M (rows of the real-embedded operand)
 constexpr int kTcBlockK = 64;    // bf16 elements per 128-byte swizzled row
 
+inline bool is_tc_precision(int precision) { return precision == MRI_BF16X3 || precision == MRI_TF32; }
+
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
@@ -78,6 +80,13 @@ struct mri_plan {
     __nv_bfloat16 *afwd_hi = nullptr, *afwd_lo = nullptr;  // [2*nk][kx]
     __nv_bfloat16 *badj_hi = nullptr, *badj_lo = nullptr;  // [ny_pad][kk]
     __nv_bfloat16 *bfwd_hi = nullptr, *bfwd_lo = nullptr;  // [nc*ny_pad][kx]
+    // TF32 form: the same operands as single TF32-rounded FP32 matrices
+    float *afwd_t = nullptr;  // [2*nk][kx]
+    float *badj_t = nullptr;  // [ny_pad][kk]
+    float *bfwd_t = nullptr;  // [nc*ny_pad][kx]
+    // tensor maps of the operands; in the TF32 form the _hi and _lo maps are
+    // the same map, and a K block's two 128-byte halves are its columns
+    // [64 kb, 64 kb + 32) and [64 kb + 32, 64 kb + 64)
     CUtensorMap tm_afwd_hi, tm_afwd_lo, tm_bfwd_hi, tm_bfwd_lo, tm_badj_hi, tm_badj_lo;
     CUtensorMap tm_axT, tm_y, tm_ayT;  // FP32 views of axT, y, ayT for staged factor tiles
 

@@ -1,4 +1,5 @@
-// BF16x3 tensor-core form of the two DFT products (tcgen05 + TMA, sm_103a).
+// Tensor-core forms of the two DFT products (tcgen05 + TMA, sm_103a): BF16x3
+// and TF32.
 //
 // Complex products are real-embedded so that one real GEMM carries them:
 // a complex row a of the left operand becomes two real rows (Re a, -Im a) and
@@ -6,7 +7,12 @@
 // interleaved along K, and output rows 2r, 2r+1 are Re and Im of row r.
 // Every FP32 operand v is split into hi = bf16(v) and lo = bf16(v - hi); the
 // product is accumulated in FP32 (TMEM) as hi*hi + hi*lo + lo*hi (the paper's
-// "decomposition and accumulation" on bf16 multipliers, Section II-A).
+// "decomposition and accumulation" on bf16 multipliers, Section II-A).  The
+// TF32 form instead rounds every operand to TF32 and issues one kind::tf32
+// product; its operands take the same bytes (a K block of 64 elements is two
+// 128-byte rows, where BF16x3 has a hi row and a lo row), so both forms share
+// the tiles, rings and stage sizes and differ only in the operand words and
+// the UMMA issue (kTf32 template parameter).
 //
 // Forward  (Eq. 1):  Z = A_x (S_c . X) for all coils at once
 //     A  = embedded A_x          [2 nk][kx]        static, TMA
@@ -58,6 +64,10 @@ constexpr int kAdjThreads = 32 * (kAdjProducerWarps + 6);
 constexpr int kMaxSmem = 227 * 1024;
 constexpr int kSmemSlack = 1024 + 256;            // alignment + barriers
 constexpr int kMaxCoilsPerTile = 4;
+#ifndef MRI_ADJ_MAX_KB_PER_SPLIT
+#define MRI_ADJ_MAX_KB_PER_SPLIT 32
+#endif
+constexpr int kMaxKbPerSplit = MRI_ADJ_MAX_KB_PER_SPLIT;  // adjoint: K blocks (32 samples each) per k-space split
 
 // Work split of both kernels: clusters of `cm` CTAs process groups of cm
 // tiles (units) in lockstep; the operand shared by the group (B) is loaded
@@ -132,12 +142,13 @@ struct Ring {
 };
 
 // ---------------------------------------------------------------------------
-// Forward operand: B[(c*ny_pad + j)][2i + {0,1}] = split(Re, Im of S_c[i][j] x[i][j])
-// block (32, 8) over a 32 x 32 (i, j) tile of coil blockIdx.z, transposed
-// through shared memory.
+// Forward operand: B[(c*ny_pad + j)][2i + {0,1}] = (Re, Im) of S_c[i][j] x[i][j],
+// split into hi/lo (BF16x3) or rounded to TF32 (t32); block (32, 8) over a
+// 32 x 32 (i, j) tile of coil blockIdx.z, transposed through shared memory.
+template <bool kTf32>
 __global__ void fwd_operand_kernel(const float2 *__restrict__ x, const float2 *__restrict__ maps,
-                                   uint32_t *__restrict__ hi, uint32_t *__restrict__ lo, int nx, int ny, int ny_pad,
-                                   int kx, const DevScalars *sc, int skip) {
+                                   uint32_t *__restrict__ hi, uint32_t *__restrict__ lo, uint2 *__restrict__ t32,
+                                   int nx, int ny, int ny_pad, int kx, const DevScalars *sc, int skip) {
     if (should_skip(sc, skip)) return;
     __shared__ float2 ts[32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -156,16 +167,21 @@ __global__ void fwd_operand_kernel(const float2 *__restrict__ x, const float2 *_
         const int j = j0 + ty + 8 * q, i = i0 + tx;
         if (i < nx && j < ny) {
             const float2 v = ts[tx][ty + 8 * q];
-            uint32_t h, l;
-            split2(v.x, v.y, h, l);
             const size_t off = ((size_t)c * ny_pad + j) * (kx / 2) + i;
-            hi[off] = h;
-            lo[off] = l;
+            if constexpr (kTf32) {
+                t32[off] = make_uint2(tf32_bits(v.x), tf32_bits(v.y));
+            } else {
+                uint32_t h, l;
+                split2(v.x, v.y, h, l);
+                hi[off] = h;
+                lo[off] = l;
+            }
         }
     }
 }
 
 // ---------------------------------------------------------------------------
+template <bool kTf32>
 __global__ void __launch_bounds__(kFwdThreads, 1)
     fwd_tc_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
                   const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
@@ -238,15 +254,17 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                     const uint32_t sbase = smem_u32(smem + (size_t)rg.stage * stage_bytes);
                     const uint32_t fb = full0 + 8 * rg.stage;
                     mbar_arrive_expect_tx(fb, stage_bytes);
-                    tma_load_2d(sbase, &ta_hi, fb, kb * kTcBlockK, m_blk * kTcBlockM);
-                    tma_load_2d(sbase + kTileBytesA, &ta_lo, fb, kb * kTcBlockK, m_blk * kTcBlockM);
+                    // BF16x3: hi and lo rows of K block kb; TF32: its two 32-element halves
+                    const int x0 = kb * kTcBlockK, x1 = x0 + (kTf32 ? kTcBlockK / 2 : 0);
+                    tma_load_2d(sbase, &ta_hi, fb, x0, m_blk * kTcBlockM);
+                    tma_load_2d(sbase + kTileBytesA, &ta_lo, fb, x1, m_blk * kTcBlockM);
                     const uint32_t bh = sbase + 2 * kTileBytesA + rank * b_slice;
                     if (P.cm > 1) {
-                        tma_load_2d_multicast(bh, &tb_hi, fb, kb * kTcBlockK, b_row, mask);
-                        tma_load_2d_multicast(bh + b_bytes, &tb_lo, fb, kb * kTcBlockK, b_row, mask);
+                        tma_load_2d_multicast(bh, &tb_hi, fb, x0, b_row, mask);
+                        tma_load_2d_multicast(bh + b_bytes, &tb_lo, fb, x1, b_row, mask);
                     } else {
-                        tma_load_2d(bh, &tb_hi, fb, kb * kTcBlockK, b_row);
-                        tma_load_2d(bh + b_bytes, &tb_lo, fb, kb * kTcBlockK, b_row);
+                        tma_load_2d(bh, &tb_hi, fb, x0, b_row);
+                        tma_load_2d(bh + b_bytes, &tb_lo, fb, x1, b_row);
                     }
                     issued_phase[rg.stage] = rg.phase;
                     issued_mask |= 1 << rg.stage;
@@ -260,7 +278,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     } else if (warp == 1) {
         // UMMA issuer
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16_f32(kTcBlockM, P.block_n);
+            const uint32_t idesc = kTf32 ? idesc_tf32_f32(kTcBlockM, P.block_n) : idesc_bf16_f32(kTcBlockM, P.block_n);
             Ring rg;
             int lt = 0;
             bool issued_any = false;
@@ -281,14 +299,25 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                     const uint32_t sa_lo = sa_hi + kTileBytesA;
                     const uint32_t sb_hi = sa_hi + 2 * kTileBytesA;
                     const uint32_t sb_lo = sb_hi + b_bytes;
+                    if constexpr (kTf32) {
+                        // eight K steps of 8 TF32 elements: four in each 128-byte half
 #pragma unroll
-                    for (int kk = 0; kk < kTcBlockK / 16; ++kk) {
-                        const uint32_t off = kk * 32;
-                        const uint64_t dah = sdesc_kmajor_sw128(sa_hi + off), dal = sdesc_kmajor_sw128(sa_lo + off);
-                        const uint64_t dbh = sdesc_kmajor_sw128(sb_hi + off), dbl = sdesc_kmajor_sw128(sb_lo + off);
-                        umma_f16(d_tmem, dah, dbh, idesc, (kb | kk) != 0);
-                        umma_f16(d_tmem, dah, dbl, idesc, 1u);
-                        umma_f16(d_tmem, dal, dbh, idesc, 1u);
+                        for (int kk = 0; kk < 8; ++kk) {
+                            const uint32_t off = (kk & 3) * 32;
+                            const uint64_t da = sdesc_kmajor_sw128((kk < 4 ? sa_hi : sa_lo) + off);
+                            const uint64_t db = sdesc_kmajor_sw128((kk < 4 ? sb_hi : sb_lo) + off);
+                            umma_tf32(d_tmem, da, db, idesc, (kb | kk) != 0);
+                        }
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < kTcBlockK / 16; ++kk) {
+                            const uint32_t off = kk * 32;
+                            const uint64_t dah = sdesc_kmajor_sw128(sa_hi + off), dal = sdesc_kmajor_sw128(sa_lo + off);
+                            const uint64_t dbh = sdesc_kmajor_sw128(sb_hi + off), dbl = sdesc_kmajor_sw128(sb_lo + off);
+                            umma_f16(d_tmem, dah, dbh, idesc, (kb | kk) != 0);
+                            umma_f16(d_tmem, dah, dbl, idesc, 1u);
+                            umma_f16(d_tmem, dal, dbh, idesc, 1u);
+                        }
                     }
                     issued_any = true;
                     // the stage is free only when every CTA of the cluster has consumed it
@@ -421,7 +450,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 // the producer warps straight into tensor memory with tcgen05.st; the UMMAs
 // read it from there (A in TMEM) and only the static conj(A_y) operand goes
 // through shared memory.  TMEM columns: n_acc accumulators of ny_pad columns,
-// then `stages` A slots of 64 columns (32 hi, 32 lo) starting at a_col0.
+// then `stages` A slots of 64 columns (BF16x3: 32 hi, 32 lo, two bf16 per
+// column; TF32: the 64 K elements, one per column) starting at a_col0.
+template <bool kTf32>
 __global__ void __launch_bounds__(kAdjThreads, 1)
     adj_tc_kernel(const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
                   const __grid_constant__ CUtensorMap t_axT, const __grid_constant__ CUtensorMap t_y,
@@ -512,12 +543,13 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                     const uint32_t sb = smem_u32(smem + (size_t)rs.stage * stage_bytes) + rank * b_slice;
                     const int b_row = rank * (P.ny_pad / P.cm);
                     mbar_arrive_expect_tx(fb, 2u * b_bytes);
+                    const int x0 = kb * kTcBlockK, x1 = x0 + (kTf32 ? kTcBlockK / 2 : 0);
                     if (P.cm > 1) {
-                        tma_load_2d_multicast(sb, &tb_hi, fb, kb * kTcBlockK, b_row, mask);
-                        tma_load_2d_multicast(sb + b_bytes, &tb_lo, fb, kb * kTcBlockK, b_row, mask);
+                        tma_load_2d_multicast(sb, &tb_hi, fb, x0, b_row, mask);
+                        tma_load_2d_multicast(sb + b_bytes, &tb_lo, fb, x1, b_row, mask);
                     } else {
-                        tma_load_2d(sb, &tb_hi, fb, kb * kTcBlockK, b_row);
-                        tma_load_2d(sb + b_bytes, &tb_lo, fb, kb * kTcBlockK, b_row);
+                        tma_load_2d(sb, &tb_hi, fb, x0, b_row);
+                        tma_load_2d(sb + b_bytes, &tb_lo, fb, x1, b_row);
                     }
                     issued_phase[rs.stage] = rs.phase;
                     issued_mask |= 1 << rs.stage;
@@ -527,34 +559,69 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                 const uint8_t *arow = raw + (size_t)rr.stage * kRawBytes + kh * (kRawBytes / 2) + ii * 128;
                 const float4 *yv4 =
                     reinterpret_cast<const float4 *>(yraw + (size_t)rr.stage * kRawYBytes + kh * 128);
-                uint32_t hre[8], lre[8], him[8], lim[8];
+                const uint32_t acol = (uint32_t)(P.a_col0 + 64 * rs.stage + (kTf32 ? 32 : 16) * kh);
+                if constexpr (kTf32) {
+                    // this thread's eight samples: Re-row pairs (ur, -ui) and Im-row pairs (ui, ur)
+                    uint32_t rw[16], iw[16];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int chunk = 4 * o + c;
-                    const float4 av = *reinterpret_cast<const float4 *>(arow + ((chunk ^ (ii & 7)) << 4));
-                    const float4 yv = yv4[chunk];
-                    split_embed(cmulc(make_float2(av.x, av.y), make_float2(yv.x, yv.y)), hre[2 * c], lre[2 * c],
-                                him[2 * c], lim[2 * c]);
-                    split_embed(cmulc(make_float2(av.z, av.w), make_float2(yv.z, yv.w)), hre[2 * c + 1],
-                                lre[2 * c + 1], him[2 * c + 1], lim[2 * c + 1]);
-                }
-                mbar_arrive(rempty0 + 8 * rr.stage);
-                rr.next(R);
-                // the Re-row thread keeps its Re words and receives the
-                // partner's; the Im-row thread likewise, in sample order
-                uint32_t hi[16], lo[16];
+                    for (int c = 0; c < 4; ++c) {
+                        const int chunk = 4 * o + c;
+                        const float4 av = *reinterpret_cast<const float4 *>(arow + ((chunk ^ (ii & 7)) << 4));
+                        const float4 yv = yv4[chunk];
+                        const float2 u0 = cmulc(make_float2(av.x, av.y), make_float2(yv.x, yv.y));
+                        const float2 u1 = cmulc(make_float2(av.z, av.w), make_float2(yv.z, yv.w));
+                        const uint32_t r0 = tf32_bits(u0.x), i0 = tf32_bits(u0.y);
+                        const uint32_t r1 = tf32_bits(u1.x), i1 = tf32_bits(u1.y);
+                        rw[4 * c] = r0;
+                        rw[4 * c + 1] = i0 ^ 0x80000000u;
+                        rw[4 * c + 2] = r1;
+                        rw[4 * c + 3] = i1 ^ 0x80000000u;
+                        iw[4 * c] = i0;
+                        iw[4 * c + 1] = r0;
+                        iw[4 * c + 2] = i1;
+                        iw[4 * c + 3] = r1;
+                    }
+                    mbar_arrive(rempty0 + 8 * rr.stage);
+                    rr.next(R);
+                    // the Re-row thread (o = 0) keeps its Re pairs and receives the
+                    // partner's; the Im-row thread likewise, in sample order
+                    uint32_t w[32];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const uint32_t rh = __shfl_xor_sync(0xffffffffu, o ? hre[e] : him[e], 1);
-                    const uint32_t rl = __shfl_xor_sync(0xffffffffu, o ? lre[e] : lim[e], 1);
-                    hi[e] = o ? rh : hre[e];
-                    lo[e] = o ? rl : lre[e];
-                    hi[8 + e] = o ? him[e] : rh;
-                    lo[8 + e] = o ? lim[e] : rl;
+                    for (int e = 0; e < 16; ++e) {
+                        const uint32_t rcv = __shfl_xor_sync(0xffffffffu, o ? rw[e] : iw[e], 1);
+                        w[e] = o ? rcv : rw[e];
+                        w[16 + e] = o ? iw[e] : rcv;
+                    }
+                    tmem_st_32cols(tmem_base + lane_base + acol, w);
+                } else {
+                    uint32_t hre[8], lre[8], him[8], lim[8];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int chunk = 4 * o + c;
+                        const float4 av = *reinterpret_cast<const float4 *>(arow + ((chunk ^ (ii & 7)) << 4));
+                        const float4 yv = yv4[chunk];
+                        split_embed(cmulc(make_float2(av.x, av.y), make_float2(yv.x, yv.y)), hre[2 * c],
+                                    lre[2 * c], him[2 * c], lim[2 * c]);
+                        split_embed(cmulc(make_float2(av.z, av.w), make_float2(yv.z, yv.w)), hre[2 * c + 1],
+                                    lre[2 * c + 1], him[2 * c + 1], lim[2 * c + 1]);
+                    }
+                    mbar_arrive(rempty0 + 8 * rr.stage);
+                    rr.next(R);
+                    // the Re-row thread keeps its Re words and receives the
+                    // partner's; the Im-row thread likewise, in sample order
+                    uint32_t hi[16], lo[16];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const uint32_t rh = __shfl_xor_sync(0xffffffffu, o ? hre[e] : him[e], 1);
+                        const uint32_t rl = __shfl_xor_sync(0xffffffffu, o ? lre[e] : lim[e], 1);
+                        hi[e] = o ? rh : hre[e];
+                        lo[e] = o ? rl : lre[e];
+                        hi[8 + e] = o ? him[e] : rh;
+                        lo[8 + e] = o ? lim[e] : rl;
+                    }
+                    tmem_st_16cols(tmem_base + lane_base + acol, hi);
+                    tmem_st_16cols(tmem_base + lane_base + acol + 32, lo);
                 }
-                const uint32_t acol = (uint32_t)(P.a_col0 + 64 * rs.stage + 16 * kh);
-                tmem_st_16cols(tmem_base + lane_base + acol, hi);
-                tmem_st_16cols(tmem_base + lane_base + acol + 32, lo);
                 tmem_wait_st();
                 fence_before_sync();
                 mbar_arrive(fb);
@@ -568,7 +635,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
     } else if (warp == kAdjMmaWarp) {
         // UMMA issuer
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16_f32(kTcBlockM, P.ny_pad);
+            const uint32_t idesc = kTf32 ? idesc_tf32_f32(kTcBlockM, P.ny_pad) : idesc_bf16_f32(kTcBlockM, P.ny_pad);
             Ring rg;
             int lt = 0;
             bool issued_any = false;
@@ -592,12 +659,22 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                     const uint32_t ta_lo = ta_hi + 32;
                     const uint32_t sb_hi = smem_u32(smem + (size_t)rg.stage * stage_bytes);
                     const uint32_t sb_lo = sb_hi + b_bytes;
+                    if constexpr (kTf32) {
+                        // K element e of the block in TMEM column e; B halves of 32 elements
 #pragma unroll
-                    for (int kk = 0; kk < kTcBlockK / 16; ++kk) {
-                        const uint64_t dbh = sdesc_kmajor_sw128(sb_hi + kk * 32), dbl = sdesc_kmajor_sw128(sb_lo + kk * 32);
-                        umma_f16_tmem_a(d_tmem, ta_hi + 8 * kk, dbh, idesc, (kb != kb0 || kk != 0) ? 1u : 0u);
-                        umma_f16_tmem_a(d_tmem, ta_hi + 8 * kk, dbl, idesc, 1u);
-                        umma_f16_tmem_a(d_tmem, ta_lo + 8 * kk, dbh, idesc, 1u);
+                        for (int kk = 0; kk < 8; ++kk) {
+                            const uint64_t db = sdesc_kmajor_sw128((kk < 4 ? sb_hi : sb_lo) + (kk & 3) * 32);
+                            umma_tf32_tmem_a(d_tmem, ta_hi + 8 * kk, db, idesc, (kb != kb0 || kk != 0) ? 1u : 0u);
+                        }
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < kTcBlockK / 16; ++kk) {
+                            const uint64_t dbh = sdesc_kmajor_sw128(sb_hi + kk * 32),
+                                           dbl = sdesc_kmajor_sw128(sb_lo + kk * 32);
+                            umma_f16_tmem_a(d_tmem, ta_hi + 8 * kk, dbh, idesc, (kb != kb0 || kk != 0) ? 1u : 0u);
+                            umma_f16_tmem_a(d_tmem, ta_hi + 8 * kk, dbl, idesc, 1u);
+                            umma_f16_tmem_a(d_tmem, ta_lo + 8 * kk, dbh, idesc, 1u);
+                        }
                     }
                     issued_any = true;
                     // the stage is free only when every CTA of the cluster has consumed it
@@ -730,6 +807,23 @@ bool make_bf16_map(CUtensorMap *m, void *base, uint64_t cols, uint64_t rows, uin
                     CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
+// TF32 operand matrix (FP32 words): boxes of 32 elements (128 bytes) x box_rows.
+bool make_tf32_map(CUtensorMap *m, void *base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+    return make_map(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, cols, rows, kTcBlockK / 2, box_rows,
+                    CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+// hi/lo maps of one operand: two BF16 matrices, or the same TF32 map twice.
+bool make_operand_maps(const mri_plan *p, CUtensorMap *hi, CUtensorMap *lo, void *bhi, void *blo, void *t32,
+                       uint64_t cols, uint64_t rows, uint32_t box_rows) {
+    if (p->precision == MRI_TF32) {
+        if (!make_tf32_map(hi, t32, cols, rows, box_rows)) return false;
+        *lo = *hi;
+        return true;
+    }
+    return make_bf16_map(hi, bhi, cols, rows, box_rows) && make_bf16_map(lo, blo, cols, rows, box_rows);
+}
+
 uint32_t tmem_cols_for(int cols) {
     uint32_t n = 32;
     while ((int)n < cols) n <<= 1;
@@ -798,13 +892,22 @@ int tc_plan_tiling(mri_plan *p) {
     p->fwd_n_tiles = ceil_div(p->nc, p->fwd_coils_per_tile);
     p->fwd_m_tiles = ceil_div(2 * p->nk, kTcBlockM);
     // adjoint: 64 pixels (128 embedded rows) of one coil per M tile; split K
-    // (k-space samples) so that the units fill the SMs evenly
+    // (k-space samples) so that the units fill the SMs evenly, with at most
+    // kMaxKbPerSplit K blocks per split.  The tensor-core accumulation into
+    // TMEM loses a roughly constant, same-signed fraction of an ulp of the
+    // running sum per UMMA, so its relative error grows linearly with the
+    // number of K blocks accumulated in one run (measured on the N=256,
+    // 65536-sample adjoint: 2.5e-5 at 108 blocks, 1.4e-5 at 64, 7.3e-6 at 32,
+    // 4.8e-6 at 16, against 3.9e-6 for exact accumulation of the same BF16x3
+    // products); 32 blocks keep the operator within 1e-5 for any nk at a
+    // cost of 6% on that adjoint (more partial images to write and sum)
     p->adj_m_tiles = p->nc * (p->nx_pad / 64);
     p->adj_block_n = p->ny_pad;
     const int num_kb = p->kk / kTcBlockK;
     long best_cost = -1;
     int best_split = 1;
-    for (int split = 1; split <= std::min(num_kb, 128); ++split) {
+    const int min_split = std::min(128, ceil_div(num_kb, kMaxKbPerSplit));
+    for (int split = min_split; split <= std::min(num_kb, 128); ++split) {
         const int per = ceil_div(num_kb, split);
         const int eff = ceil_div(num_kb, per);
         const long waves = ceil_div(p->adj_m_tiles * eff, p->num_sms);
@@ -827,8 +930,8 @@ int tc_plan_tiling(mri_plan *p) {
 
 int tc_make_tensor_maps(mri_plan *p) {
     const uint64_t nkf = 2ull * p->nk_pad;  // floats per sample-indexed row
-    bool ok = make_bf16_map(&p->tm_afwd_hi, p->afwd_hi, p->kx, 2ull * p->nk, kTcBlockM) &&
-              make_bf16_map(&p->tm_afwd_lo, p->afwd_lo, p->kx, 2ull * p->nk, kTcBlockM) &&
+    bool ok = make_operand_maps(p, &p->tm_afwd_hi, &p->tm_afwd_lo, p->afwd_hi, p->afwd_lo, p->afwd_t, p->kx,
+                                2ull * p->nk, kTcBlockM) &&
               make_map(&p->tm_axT, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->axT, nkf, p->nx, 32, 64,
                        CU_TENSOR_MAP_SWIZZLE_128B) &&
               make_map(&p->tm_y, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->y, nkf, p->nc, 64, 1,
@@ -839,9 +942,13 @@ int tc_make_tensor_maps(mri_plan *p) {
         set_error("cuTensorMapEncodeTiled failed");
         return MRI_ERR_CUDA;
     }
-    cudaError_t e = cudaFuncSetAttribute(fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaError_t e = cudaFuncSetAttribute(fwd_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(adj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        e = cudaFuncSetAttribute(fwd_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(adj_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(adj_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     if (e != cudaSuccess) {
         set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
         return MRI_ERR_CUDA;
@@ -912,10 +1019,10 @@ int tc_set_clusters(mri_plan *p, int fwd_cm, int adj_cm) {
         return MRI_ERR_INVALID;
     }
     // the shared B operand is fetched in cm row slices, one per CTA of the cluster
-    bool ok = make_bf16_map(&p->tm_bfwd_hi, p->bfwd_hi, p->kx, (uint64_t)p->nc * p->ny_pad, p->fwd_block_n / fwd_cm) &&
-              make_bf16_map(&p->tm_bfwd_lo, p->bfwd_lo, p->kx, (uint64_t)p->nc * p->ny_pad, p->fwd_block_n / fwd_cm) &&
-              make_bf16_map(&p->tm_badj_hi, p->badj_hi, p->kk, p->ny_pad, p->ny_pad / adj_cm) &&
-              make_bf16_map(&p->tm_badj_lo, p->badj_lo, p->kk, p->ny_pad, p->ny_pad / adj_cm);
+    bool ok = make_operand_maps(p, &p->tm_bfwd_hi, &p->tm_bfwd_lo, p->bfwd_hi, p->bfwd_lo, p->bfwd_t, p->kx,
+                                (uint64_t)p->nc * p->ny_pad, p->fwd_block_n / fwd_cm) &&
+              make_operand_maps(p, &p->tm_badj_hi, &p->tm_badj_lo, p->badj_hi, p->badj_lo, p->badj_t, p->kk,
+                                p->ny_pad, p->ny_pad / adj_cm);
     if (!ok) {
         set_error("cuTensorMapEncodeTiled failed");
         return MRI_ERR_CUDA;
@@ -927,16 +1034,25 @@ int tc_set_clusters(mri_plan *p, int fwd_cm, int adj_cm) {
     size_t fsm, asm_;
     fwd_smem_plan(p, &s, &r, &fsm);
     adj_smem_plan(p, &s, &r, &asm_);
-    p->fwd_grid = fwd_cm * resident_clusters(fwd_tc_kernel, kFwdThreads, fsm, fwd_cm, p->num_sms);
-    p->adj_grid = adj_cm * resident_clusters(adj_tc_kernel, kAdjThreads, asm_, adj_cm, p->num_sms);
+    const bool t = p->precision == MRI_TF32;
+    p->fwd_grid = fwd_cm * (t ? resident_clusters(fwd_tc_kernel<true>, kFwdThreads, fsm, fwd_cm, p->num_sms)
+                              : resident_clusters(fwd_tc_kernel<false>, kFwdThreads, fsm, fwd_cm, p->num_sms));
+    p->adj_grid = adj_cm * (t ? resident_clusters(adj_tc_kernel<true>, kAdjThreads, asm_, adj_cm, p->num_sms)
+                              : resident_clusters(adj_tc_kernel<false>, kAdjThreads, asm_, adj_cm, p->num_sms));
     return MRI_OK;
 }
 
 cudaError_t launch_fwd_tc(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace, int ld, int skip,
                           cudaStream_t s) {
+    const bool t = p->precision == MRI_TF32;
     dim3 og(ceil_div(p->nx, 32), ceil_div(p->ny, 32), p->nc);
-    fwd_operand_kernel<<<og, dim3(32, 8), 0, s>>>(image, maps, (uint32_t *)p->bfwd_hi, (uint32_t *)p->bfwd_lo, p->nx,
-                                                  p->ny, p->ny_pad, p->kx, p->scal, skip);
+    if (t)
+        fwd_operand_kernel<true><<<og, dim3(32, 8), 0, s>>>(image, maps, nullptr, nullptr, (uint2 *)p->bfwd_t, p->nx,
+                                                            p->ny, p->ny_pad, p->kx, p->scal, skip);
+    else
+        fwd_operand_kernel<false><<<og, dim3(32, 8), 0, s>>>(image, maps, (uint32_t *)p->bfwd_hi,
+                                                             (uint32_t *)p->bfwd_lo, nullptr, p->nx, p->ny,
+                                                             p->ny_pad, p->kx, p->scal, skip);
     FwdParams P;
     P.y = kspace;
     P.y_ld = ld;
@@ -957,8 +1073,10 @@ cudaError_t launch_fwd_tc(mri_plan *p, const float2 *image, const float2 *maps, 
     P.status = &p->scal->status;
     const int grid = P.cm * std::min(P.num_groups, p->fwd_grid / P.cm);
     timing_begin(p, s);
-    cudaError_t e = launch_clustered(fwd_tc_kernel, grid, kFwdThreads, smem, P.cm, s, p->tm_afwd_hi, p->tm_afwd_lo,
-                                     p->tm_bfwd_hi, p->tm_bfwd_lo, p->tm_ayT, P);
+    cudaError_t e = t ? launch_clustered(fwd_tc_kernel<true>, grid, kFwdThreads, smem, P.cm, s, p->tm_afwd_hi,
+                                         p->tm_afwd_lo, p->tm_bfwd_hi, p->tm_bfwd_lo, p->tm_ayT, P)
+                      : launch_clustered(fwd_tc_kernel<false>, grid, kFwdThreads, smem, P.cm, s, p->tm_afwd_hi,
+                                         p->tm_afwd_lo, p->tm_bfwd_hi, p->tm_bfwd_lo, p->tm_ayT, P);
     timing_end(p, s);
     p->launches += 2;
     return e != cudaSuccess ? e : cudaGetLastError();
@@ -986,8 +1104,11 @@ cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
     P.status = &p->scal->status;
     const int grid = P.cm * std::min(P.num_groups, p->adj_grid / P.cm);
     timing_begin(p, s);
-    cudaError_t e = launch_clustered(adj_tc_kernel, grid, kAdjThreads, smem, P.cm, s, p->tm_badj_hi, p->tm_badj_lo,
-                                     p->tm_axT, p->tm_y, P);
+    cudaError_t e = p->precision == MRI_TF32
+                        ? launch_clustered(adj_tc_kernel<true>, grid, kAdjThreads, smem, P.cm, s, p->tm_badj_hi,
+                                           p->tm_badj_lo, p->tm_axT, p->tm_y, P)
+                        : launch_clustered(adj_tc_kernel<false>, grid, kAdjThreads, smem, P.cm, s, p->tm_badj_hi,
+                                           p->tm_badj_lo, p->tm_axT, p->tm_y, P);
     timing_end(p, s);
     p->launches += 1;
     return e != cudaSuccess ? e : cudaGetLastError();

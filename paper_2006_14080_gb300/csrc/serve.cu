@@ -309,7 +309,7 @@ MRI_API int mri_server_create(mri_server **out, size_t hbm_budget_bytes, int max
     *out = nullptr;
     if (hbm_budget_bytes == 0 || max_inflight <= 0 || max_inflight > 64)
         return set_error("budget must be > 0 and max_inflight in 1..64"), MRI_ERR_INVALID;
-    if (precision != MRI_FP32 && precision != MRI_BF16X3) return set_error("unknown precision"), MRI_ERR_INVALID;
+    if (precision != MRI_FP32 && !is_tc_precision(precision)) return set_error("unknown precision"), MRI_ERR_INVALID;
     mri_server *s = new mri_server();
     s->budget = hbm_budget_bytes;
     s->max_inflight = max_inflight;

@@ -1,7 +1,8 @@
 // Inline-PTX wrappers for the sm_103a tensor-core path: mbarriers with
 // bounded waits, 2-D TMA tile loads, and the tcgen05 family (TMEM
-// allocation, UMMA issue/commit, TMEM loads), plus the UMMA shared-memory
-// and instruction descriptors for K-major, 128-byte-swizzled BF16 operands.
+// allocation, UMMA issue/commit, TMEM loads and stores), plus the UMMA
+// shared-memory and instruction descriptors for K-major, 128-byte-swizzled
+// BF16 and TF32 operands.
 #pragma once
 
 #include <cuda.h>
@@ -124,6 +125,16 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a_desc, uint6
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::tf32 (TF32 inputs in 32-bit words, FP32 accumulator)
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 // Arrive once on the mbarrier when all previously issued UMMAs of this thread completed.
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -166,6 +177,31 @@ __device__ __forceinline__ void umma_f16_tmem_a(uint32_t d_tmem, uint32_t a_tmem
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
         "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// D[tmem] (+)= A[tmem] * B[smem]^T, kind::tf32: A read from tensor memory
+// (row m in lane m, one TF32 K-element per 32-bit column).
+__device__ __forceinline__ void umma_tf32_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                                 uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Store 32 consecutive 32-bit columns of this thread's lane (32x32b shape).
+__device__ __forceinline__ void tmem_st_32cols(uint32_t taddr, const uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+        "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]),
+        "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]),
+        "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
         : "memory");
 }
 
@@ -217,6 +253,23 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int m, int n) {
            | (1u << 10)                         // B format: BF16
            | ((uint32_t)(n >> 3) << 17)         // N >> 3
            | ((uint32_t)(m >> 4) << 24);        // M >> 4
+}
+
+// Instruction descriptor, kind::tf32: TF32 A and B (K-major), FP32 D, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32_f32(int m, int n) {
+    return (1u << 4)                            // D format: F32
+           | (2u << 7)                          // A format: TF32
+           | (2u << 10)                         // B format: TF32
+           | ((uint32_t)(n >> 3) << 17)         // N >> 3
+           | ((uint32_t)(m >> 4) << 24);        // M >> 4
+}
+
+// FP32 -> TF32 (10-bit mantissa), round to nearest with ties away from zero;
+// the result is an FP32 bit pattern whose low 13 mantissa bits are zero.
+__device__ __forceinline__ uint32_t tf32_bits(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return r;
 }
 
 // Byte offset of element (row, col) of a 128-byte-swizzled tile of bf16 rows:

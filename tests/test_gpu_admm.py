@@ -94,6 +94,19 @@ def test_admm_medium_matches_oracle(mr, precision):
     assert err <= NRMSE_TOL
 
 
+def test_admm_medium_tf32_reported(mr):
+    # The TF32 form carries ~4e-4 relative error per operator application
+    # (10-bit operand mantissas), forty times the BF16x3 form's, so it is not
+    # held to the 1e-3 image bar; it is held to the paper's ~1% FP32-vs-FP64
+    # level and its measured NRMSE is printed.
+    p = synth.config_medium()
+    g, d = _golden(p)
+    x, _, _ = _run(mr, p, d, "tf32", with_hist=False)
+    err = _nrmse(x, g["x"])
+    print(f"medium workload tf32: NRMSE vs FP64 oracle = {err:.3e}")
+    assert err <= 1e-2
+
+
 @pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 def test_admm_table1_tolerances_stop_like_oracle(mr, precision):
     with open(os.path.join(GOLDEN, "table1_admm_params.json")) as fh:

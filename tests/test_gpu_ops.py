@@ -2,10 +2,15 @@
 
 Sizes span several tiles of both product kernels with ragged tails (image
 sides not multiples of 32/64, sample counts not multiples of 64).  Bars:
-relative L2 error of the DFT operators <= 2e-6 (FP32 FFMA path) and <= 1e-5
-(BF16x3 tensor path, the operator target); the image-space stencils are
-single FP32 roundings of exact differences, so they are held to 4 ulp of the
-field's maximum.
+relative L2 error of the DFT operators <= 2e-6 (FP32 FFMA path), <= 1e-5
+(BF16x3 tensor path, the operator target) and <= 2e-3 for the TF32 tensor
+path (each operand is rounded to a 10-bit mantissa, relative error up to
+2^-11 = 4.9e-4 and about 2.8e-4 rms per operand, so a product term carries
+about 4e-4 rms and the sum of many terms with independent errors keeps that
+relative size: 2e-3 leaves a factor 5; test_gpu_tf32 checks the TF32
+kernels far more tightly against an emulation of exactly that rounding).
+The image-space stencils are single FP32 roundings of exact differences, so
+they are held to 4 ulp of the field's maximum.
 """
 import numpy as np
 import pytest
@@ -16,7 +21,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-OP_TOL = {"fp32": 2e-6, "bf16x3": 1e-5}
+OP_TOL = {"fp32": 2e-6, "bf16x3": 1e-5, "tf32": 2e-3}
 
 
 @pytest.fixture(scope="module")
@@ -54,7 +59,7 @@ SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "tf32"])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_forward_adjoint_normal_match_oracle(mr, precision, shape):
     nx, ny, nc, spokes, readout = shape
@@ -71,7 +76,7 @@ def test_forward_adjoint_normal_match_oracle(mr, precision, shape):
     assert _rel(nrm, oracle.normal(traj, maps, 0.8, x)) <= 2 * tol
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "tf32"])
 def test_cartesian_grid_gives_centred_fft(mr, precision):
     n, nc = 32, 2
     rng = np.random.default_rng(3)
@@ -85,7 +90,7 @@ def test_cartesian_grid_gives_centred_fft(mr, precision):
     assert _rel(got, ref) <= OP_TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "tf32"])
 def test_adjoint_identity_on_gpu(mr, precision):
     nx, ny, nc = 96, 80, 6
     maps, traj, x, y = _case(nx, ny, nc, 24, 160, seed=11)
@@ -124,7 +129,7 @@ def test_threshold_worked_values_eq9(mr):
         assert abs(got.real - expected) <= 1e-6 * max(1.0, abs(expected)) and got.imag == 0
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "tf32"])
 def test_degenerate_shapes(mr, precision):
     # one pixel row, one coil, a single sample
     for nx, ny, nc, nk in [(1, 1, 1, 1), (3, 17, 1, 5), (70, 1, 2, 33)]:
