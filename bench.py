@@ -453,19 +453,21 @@ def run_batch(args, rank, world, local_rank):
 
 
 def run_serve(args, rank, world, local_rank):
-    """Serving loop: heterogeneous requests (the batch item mix) arriving from
+    """Serving loop: a stream of heterogeneous requests (sizes as the batch
+    items, each with its own phantom, maps, noise and trajectory) arriving from
     host memory as a Poisson process, admitted under a device-memory budget
-    and run concurrently.  A burst of all requests first measures the
-    server's capacity (also filling its plan cache); the timed pass then
-    submits the same requests at 80% of that rate.  value = requests / (last
-    completion - first submission); latency = submission to image on host."""
+    and run concurrently.  Per precision: a burst of the first requests
+    measures the server's capacity; then each arrival rate (a multiple of that
+    capacity) gets waves of all requests.  value = requests / (last completion
+    - first submission) at the first rate, BF16x3; latency = submission to
+    image in host memory."""
     import threading
     import torch
     import paper_2006_14080_gb300 as mr
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    probs = [synth.batch_item(j) for j in range(args.serve_requests)]
+    probs = [synth.serve_request(r) for r in range(args.serve_requests)]
     reqs = []
     for p in probs:
         traj = torch.from_numpy(p.traj).to(dev)
@@ -476,14 +478,16 @@ def run_serve(args, rank, world, local_rank):
                      p.maps.astype(np.complex64), p.lam, p.beta, p.admm_iters, p.cg_iters))
     torch.cuda.synchronize()
     budget = int(args.serve_budget_gb * (1 << 30))
+    rates = [float(v) for v in args.serve_rates.split(",")]
+    precisions = args.serve_precisions.split(",")
 
-    def wave(srv, gaps):
+    def wave(srv, items, gaps):
         lat, tickets = [], []
         t0 = time.perf_counter()
 
         def feed():
             t_next = t0
-            for r, g in zip(reqs, gaps):
+            for r, g in zip(items, gaps):
                 t_next += g
                 dt = t_next - time.perf_counter()
                 if dt > 0:
@@ -492,7 +496,7 @@ def run_serve(args, rank, world, local_rank):
         th = threading.Thread(target=feed)
         th.start()
         q = 0
-        while q < len(reqs):
+        while q < len(items):
             while len(tickets) <= q:
                 time.sleep(1e-4)
             lat.append(srv.wait(tickets[q])[1])
@@ -500,34 +504,54 @@ def run_serve(args, rank, world, local_rank):
         th.join()
         return time.perf_counter() - t0, lat
 
-    with mr.Server(budget, max_inflight=args.serve_inflight, precision="bf16x3") as srv, \
-            ClockSampler(local_rank) as clk:
-        burst_s = 0.0
-        for _ in range(max(1, args.warmup)):
-            burst_s, _ = wave(srv, [0.0] * len(reqs))
-        rate = 0.8 * len(reqs) / burst_s
-        rng = np.random.default_rng(2020)
-        total_s, lats = 0.0, []
-        for _ in range(args.steps):
-            gaps = [0.0] + list(rng.exponential(1.0 / rate, len(reqs) - 1))
-            t, lat = wave(srv, gaps)
-            total_s += t
-            lats += lat
-        st = srv.stats()
-    lats.sort()
-    pct = lambda q: lats[min(len(lats) - 1, max(0, math.ceil(q * len(lats)) - 1))]  # noqa: E731
-    n = len(reqs) * args.steps
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, max(0, math.ceil(q * len(v)) - 1))]
+
+    results = {}
+    rng = np.random.default_rng(2020)
+    with ClockSampler(local_rank) as clk:
+        for prec in precisions:
+            items = reqs if prec != "fp32" else reqs[: max(1, min(len(reqs), args.serve_fp32_requests))]
+            cap_items = items[: max(1, min(len(items), args.serve_capacity_requests))]
+            with mr.Server(budget, max_inflight=args.serve_inflight, precision=prec) as srv:
+                burst_s = 0.0
+                for _ in range(max(1, args.warmup if prec != "fp32" else 1)):
+                    burst_s, _ = wave(srv, cap_items, [0.0] * len(cap_items))
+                capacity = len(cap_items) / burst_s
+                sweep = []
+                for k, mult in enumerate(rates):
+                    waves = args.steps if (k == 0 and prec != "fp32") else 1
+                    # the first rate takes every request; the rest of the sweep a prefix
+                    wave_items = items if k == 0 or args.serve_sweep_requests <= 0 else \
+                        items[: min(len(items), args.serve_sweep_requests)]
+                    total_s, lats = 0.0, []
+                    for _ in range(waves):
+                        gaps = [0.0] + list(rng.exponential(1.0 / (mult * capacity), len(wave_items) - 1))
+                        t, lat = wave(srv, wave_items, gaps)
+                        total_s += t
+                        lats += lat
+                    sweep.append({"rate_x_capacity": mult, "arrival_rate_recon_s": mult * capacity,
+                                  "requests": len(wave_items) * waves, "value": len(wave_items) * waves / total_s,
+                                  "p50_ms": pct(lats, 0.50), "p99_ms": pct(lats, 0.99), "max_ms": max(lats),
+                                  "wall_s": total_s})
+                st = srv.stats()
+            results[prec] = {"burst_capacity_recon_s": capacity, "capacity_requests": len(cap_items),
+                             "sweep": sweep, "peak_resident_bytes": st["peak_resident_bytes"]}
+    head = results[precisions[0]]["sweep"][0]
     return {
         "metric": f"served ADMM recon/s, {len(reqs)} heterogeneous requests (N 64-256, 8-32 coils, 32-200 "
-                  "golden-angle spokes x 2N, 30 ADMM x 8 CG) from host memory, Poisson arrivals at 80% of burst "
-                  "capacity, BF16x3",
-        "value": n / total_s, "unit": "recon/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16x3/f32", "data": "synthetic (seeded per item)",
-        "latency_ms": {"p50": pct(0.50), "p99": pct(0.99), "max": lats[-1]},
-        "burst_capacity_recon_s": len(reqs) / burst_s, "arrival_rate_recon_s": rate,
+                  "golden-angle spokes x 2N, 30 ADMM x 8 CG; own phantom, maps and trajectory each) from host "
+                  f"memory, Poisson arrivals at {rates[0]} x burst capacity, {precisions[0].upper()}",
+        "value": head["value"], "unit": "recon/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * head["wall_s"] / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3/f32" if precisions[0] == "bf16x3" else precisions[0],
+        "data": "synthetic (seeded per request)",
+        "latency_ms": {"p50": head["p50_ms"], "p99": head["p99_ms"], "max": head["max_ms"]},
+        "forms": results,
         "config": {"workload": f"serve{len(reqs)}_poisson", "budget_bytes": budget,
-                   "max_inflight": args.serve_inflight, "peak_resident_bytes": st["peak_resident_bytes"],
+                   "max_inflight": args.serve_inflight, "rates_x_capacity": rates,
+                   "fp32_requests": min(len(reqs), args.serve_fp32_requests),
                    "timing": "host wall clock, submit to image in host memory"},
         "clocks": clk.summary(),
     }
@@ -615,6 +639,16 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-inflight", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=32.0)
+    ap.add_argument("--serve-rates", default="0.8",
+                    help="comma list of arrival rates as multiples of the measured burst capacity")
+    ap.add_argument("--serve-precisions", default="bf16x3",
+                    help="comma list of forms to serve (bf16x3, tf32, fp32); the first is the headline")
+    ap.add_argument("--serve-capacity-requests", type=int, default=64,
+                    help="requests in the burst that measures capacity")
+    ap.add_argument("--serve-sweep-requests", type=int, default=0,
+                    help="requests per wave at the rates after the first (0: all)")
+    ap.add_argument("--serve-fp32-requests", type=int, default=24,
+                    help="requests per wave for the FP32 form (about 2 s per request)")
     ap.add_argument("--clusters", default="",
                     help="'F,A': forward and adjoint cluster sizes instead of autotuning them")
     ap.add_argument("--forms", default="",

@@ -47,18 +47,21 @@ int dev_alloc(mri_plan *p, T **ptr, size_t count) {
         *ptr = nullptr;
         return MRI_OK;
     }
-    cudaError_t e = cudaMalloc((void **)ptr, count * sizeof(T));
+    cudaError_t e = p->pool ? cudaMallocFromPoolAsync((void **)ptr, count * sizeof(T), p->pool, p->pool_stream)
+                            : cudaMalloc((void **)ptr, count * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();
         *ptr = nullptr;
-        return fail(MRI_ERR_NOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+        return fail(MRI_ERR_NOMEM, std::string("device allocation of ") + std::to_string(count * sizeof(T)) +
                                        " bytes failed: " + cudaGetErrorString(e));
     }
     p->bytes += count * sizeof(T);
     return MRI_OK;
 }
 
-void free_plan(mri_plan *p) {
+// Frees everything the plan owns; pool-allocated plans free stream-ordered on
+// free_stream (the caller guarantees no work on the plan is still pending).
+void free_plan(mri_plan *p, cudaStream_t free_stream = nullptr) {
     if (!p) return;
     invalidate_graph(p);
     void *bufs[] = {p->ax,      p->ay,      p->axT,     p->ayT,    p->afwd_hi, p->afwd_lo, p->badj_hi,
@@ -66,7 +69,12 @@ void free_plan(mri_plan *p) {
                     p->y,       p->part,    p->x,       p->xprev,  p->r,       p->d,       p->ad,
                     p->b,       p->fhd,     p->mu,      p->eta,    p->partials, p->scal};
     for (void *q : bufs)
-        if (q) cudaFree(q);
+        if (q) {
+            if (p->pool)
+                cudaFreeAsync(q, free_stream);
+            else
+                cudaFree(q);
+        }
     for (cudaEvent_t e : p->ev_free) cudaEventDestroy(e);
     for (auto *list : {&p->ev_fwd, &p->ev_adj, &p->ev_red})
         for (auto &pr : *list) {
@@ -183,8 +191,12 @@ MRI_API const char *mri_last_error(void) { return g_last_error.c_str(); }
 
 MRI_API int mri_version(void) { return 100; }
 
-MRI_API int mri_plan_create(mri_plan **out, int nx, int ny, int nk, int nc, const float *traj, int precision,
-                            mri_stream_t stream) {
+}  // extern "C"
+
+namespace mri {
+
+int plan_create(mri_plan **out, int nx, int ny, int nk, int nc, const float *traj, int precision,
+                cudaStream_t stream, cudaMemPool_t pool) {
     if (!out) return fail(MRI_ERR_INVALID, "plan output pointer is null");
     *out = nullptr;
     if (nx <= 0 || ny <= 0 || nk <= 0 || nc <= 0) return fail(MRI_ERR_INVALID, "dimensions must be positive");
@@ -195,6 +207,8 @@ MRI_API int mri_plan_create(mri_plan **out, int nx, int ny, int nk, int nc, cons
     cudaStream_t s = (cudaStream_t)stream;
 
     mri_plan *p = new mri_plan();
+    p->pool = pool;
+    p->pool_stream = s;
     p->nx = nx;
     p->ny = ny;
     p->nk = nk;
@@ -297,6 +311,17 @@ MRI_API int mri_plan_create(mri_plan **out, int nx, int ny, int nk, int nc, cons
     }
     *out = p;
     return MRI_OK;
+}
+
+void plan_destroy_async(mri_plan *p, cudaStream_t s) { free_plan(p, s); }
+
+}  // namespace mri
+
+extern "C" {
+
+MRI_API int mri_plan_create(mri_plan **out, int nx, int ny, int nk, int nc, const float *traj, int precision,
+                            mri_stream_t stream) {
+    return plan_create(out, nx, ny, nk, nc, traj, precision, (cudaStream_t)stream, nullptr);
 }
 
 MRI_API int mri_plan_set_trajectory(mri_plan *p, const float *traj, mri_stream_t stream) {

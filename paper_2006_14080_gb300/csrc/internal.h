@@ -106,6 +106,10 @@ struct mri_plan {
     mri::DevScalars *scal = nullptr;
 
     size_t bytes = 0;
+    // when set, every buffer comes from this stream-ordered pool (allocated on
+    // pool_stream) and is freed stream-ordered (see plan_destroy_async)
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t pool_stream = nullptr;
 
     // diagnostics: kernel launches issued on this plan, and optional CUDA-event
     // timing of the two product kernels (see mri_plan_set_timing)
@@ -134,6 +138,12 @@ struct mri_plan {
 };
 
 namespace mri {
+// mri_plan_create with an optional stream-ordered pool for the plan's buffers.
+int plan_create(mri_plan **out, int nx, int ny, int nk, int nc, const float *traj, int precision,
+                cudaStream_t stream, cudaMemPool_t pool);
+// Release a plan without synchronising: pool-allocated buffers are freed
+// stream-ordered on s (no work on the plan may be pending elsewhere).
+void plan_destroy_async(mri_plan *p, cudaStream_t s);
 // Drop the cached reconstruction graph (its kernels' arguments are stale).
 void invalidate_graph(mri_plan *p);
 // Argument checks of mri_admm_reconstruct (MRI_* status, sets the error text).

@@ -47,6 +47,7 @@ struct PlanEntry {
     bool busy = false;
     uint64_t last_use = 0;
     size_t bytes = 0;
+    cudaStream_t last_stream = nullptr;  // stream of the plan's last work (stream-ordered free)
 };
 
 struct Job {
@@ -58,6 +59,7 @@ struct Job {
     void *d_traj = nullptr, *d_k = nullptr, *d_maps = nullptr, *d_img = nullptr;
     size_t dev_bytes = 0;
     PlanEntry *entry = nullptr;
+    bool retarget = false;  // the entry is an idle plan of the same shape given this request's trajectory
     int slot = -1;
     cudaEvent_t done_ev = nullptr;
     Clock::time_point t_submit, t_done;
@@ -138,11 +140,20 @@ int start_job(mri_server *s, Job *j) {
         return MRI_ERR_CUDA;
     }
     PlanEntry *pe = j->entry;
+    pe->last_stream = st;
     if (!pe->plan) {
-        int rc = mri_plan_create(&pe->plan, r.nx, r.ny, r.nk, r.nc, (const float *)j->d_traj, s->precision, st);
+        // plan buffers come from the server's pool, so that evicting the plan
+        // later frees them stream-ordered instead of synchronising the device
+        int rc = mri::plan_create(&pe->plan, r.nx, r.ny, r.nk, r.nc, (const float *)j->d_traj, s->precision, st, s->pool);
         if (rc != MRI_OK) return rc;
         mri_plan_set_graphs(pe->plan, 0);  // a request's buffers are new each time: launch directly
         pe->bytes = mri_plan_device_bytes(pe->plan);
+    } else if (j->retarget) {
+        // same shape, other trajectory: regenerate the factors in place (Alg. 1)
+        pe->traj_hash = 0;
+        int rc = mri_plan_set_trajectory(pe->plan, (const float *)j->d_traj, st);
+        if (rc != MRI_OK) return rc;
+        pe->traj_hash = j->traj_hash;
     }
     int rc = mri_admm_reconstruct(pe->plan, (const mri_c64 *)j->d_k, (const mri_c64 *)j->d_maps, &r.params,
                                   (mri_c64 *)j->d_img, nullptr, nullptr, st);
@@ -177,7 +188,7 @@ void make_room(mri_server *s, size_t need) {
             if (!pe->busy && pe->plan && (!victim || pe->last_use < victim->last_use)) victim = pe;
         if (!victim) return;
         s->resident -= victim->bytes;
-        mri_plan_destroy(victim->plan);
+        mri::plan_destroy_async(victim->plan, victim->last_stream);  // idle: its last work has completed
         s->plans.erase(std::find(s->plans.begin(), s->plans.end(), victim));
         delete victim;
     }
@@ -230,15 +241,27 @@ void worker_loop(mri_server *s) {
             if (slot < 0) break;
             Job *j = s->pending.front();
             const mri_server_request &r = j->req;
-            PlanEntry *pe = nullptr;
-            for (PlanEntry *c : s->plans)
-                if (!c->busy && c->nx == r.nx && c->ny == r.ny && c->nk == r.nk && c->nc == r.nc &&
-                    c->traj_hash == j->traj_hash) {
+            // plan: an idle cached plan of this shape and trajectory; else a
+            // new one if it fits; else an idle plan of the same shape given
+            // this trajectory (no allocation); else a new one after evicting
+            PlanEntry *pe = nullptr, *same_shape = nullptr;
+            for (PlanEntry *c : s->plans) {
+                if (c->busy || c->nx != r.nx || c->ny != r.ny || c->nk != r.nk || c->nc != r.nc || !c->plan) continue;
+                if (c->traj_hash == j->traj_hash) {
                     pe = c;
                     break;
                 }
-            const size_t plan_bytes = pe ? 0 : mri_plan_estimate_bytes(r.nx, r.ny, r.nk, r.nc, s->precision);
-            const size_t need = plan_bytes + job_buffer_bytes(j);
+                if (!same_shape || c->last_use < same_shape->last_use) same_shape = c;
+            }
+            size_t plan_bytes = pe ? 0 : mri_plan_estimate_bytes(r.nx, r.ny, r.nk, r.nc, s->precision);
+            size_t need = plan_bytes + job_buffer_bytes(j);
+            j->retarget = false;
+            if (!pe && same_shape && s->resident + need > s->budget) {
+                pe = same_shape;
+                j->retarget = true;
+                plan_bytes = 0;
+                need = job_buffer_bytes(j);
+            }
             if ((!pe && plan_bytes == 0) || need > s->budget) {
                 s->pending.pop_front();
                 fail_job(s, j, MRI_ERR_NOMEM,

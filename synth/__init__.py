@@ -43,13 +43,14 @@ def pixel_coords(n: int) -> np.ndarray:
     return np.arange(n, dtype=np.float64) - (n // 2)
 
 
-def radial_trajectory(spokes: int, readout: int, golden: bool = True) -> np.ndarray:
-    """Radial k-space trajectory, float32 ``[spokes*readout][2]`` in cycles/pixel."""
+def radial_trajectory(spokes: int, readout: int, golden: bool = True, rotation: float = 0.0) -> np.ndarray:
+    """Radial k-space trajectory, float32 ``[spokes*readout][2]`` in cycles/pixel;
+    every spoke angle is offset by ``rotation`` radians."""
     r = (np.arange(readout, dtype=np.float64) - readout / 2.0) / readout
     if golden:
-        theta = np.arange(spokes, dtype=np.float64) * GOLDEN_ANGLE
+        theta = rotation + np.arange(spokes, dtype=np.float64) * GOLDEN_ANGLE
     else:
-        theta = np.arange(spokes, dtype=np.float64) * (math.pi / spokes)
+        theta = rotation + np.arange(spokes, dtype=np.float64) * (math.pi / spokes)
     kx = np.outer(np.cos(theta), r).reshape(-1)
     ky = np.outer(np.sin(theta), r).reshape(-1)
     return np.stack([kx, ky], axis=1).astype(np.float32)
@@ -210,6 +211,25 @@ def batch_item(j: int) -> Problem:
     traj = radial_trajectory(spokes, 2 * n, golden=True)
     return Problem(f"batch{j}_n{n}_c{nc}_s{spokes}", n, n, nc, spokes, 2 * n, traj, img, maps,
                    noise, 0.005, 1e-3, 1.0, 30, 8, 4000 + j)
+
+
+def serve_request(r: int) -> Problem:
+    """Request ``r`` of the serving stream: sizes drawn as for the batch items
+    (N in {64,128,192,256}, coils in {8,16,32}, 32..200 golden-angle spokes of
+    2N samples, 30 ADMM x 8 CG), each with its own seeded phantom, coil maps,
+    noise and trajectory (golden-angle spokes from a seeded starting angle)."""
+    rng = np.random.default_rng(500000 + r)
+    n = int(rng.choice([64, 128, 192, 256]))
+    nc = int(rng.choice([8, 16, 32]))
+    spokes = int(rng.integers(32, 201))
+    rotation = float(rng.uniform(0.0, math.pi))
+    ell = random_ellipses(rng, n, n)
+    img = rasterize(ell, n, n)
+    maps = coil_maps(rng, n, n, nc)
+    noise = unit_noise(rng, nc, spokes * 2 * n)
+    traj = radial_trajectory(spokes, 2 * n, golden=True, rotation=rotation)
+    return Problem(f"req{r}_n{n}_c{nc}_s{spokes}", n, n, nc, spokes, 2 * n, traj, img, maps,
+                   noise, 0.005, 1e-3, 1.0, 30, 8, 500000 + r)
 
 
 def random_complex(rng: np.random.Generator, shape, dtype=np.complex64) -> np.ndarray:

@@ -135,3 +135,29 @@ def test_serve_rejects_bad_requests(mr):
         with pytest.raises(ValueError):
             srv.submit(np.zeros((10, 2), np.float32), np.zeros((2, 9), np.complex64), np.zeros((2, 8, 8), np.complex64),
                        1e-3, 1.0, 1, 1)
+
+
+def test_serve_retargets_idle_plan_of_same_shape(mr):
+    # four requests of one shape with different trajectories and a budget for
+    # one plan: the server must regenerate the idle plan's factors in place
+    # (no allocation) and still give each request its alone result
+    base = synth.make_problem("s48r", 48, 3, 12, 96, seed=7201, golden=True, noise_level=0.01,
+                              admm_iters=4, cg_iters=3)
+    reqs = []
+    for q in range(4):
+        traj = synth.radial_trajectory(12, 96, golden=True, rotation=0.37 * q)
+        d = synth.add_noise(oracle.forward(traj, base.image_true, base.maps), base.noise, base.noise_level)
+        reqs.append((traj, d))
+    one = mr.estimate_plan_bytes(48, 48, base.nk, base.nc, "bf16x3") + \
+        8 * (base.nk * base.nc + base.nc * 48 * 48 + base.nk + 48 * 48)
+    with mr.Server(one + one // 2, max_inflight=2) as srv:
+        tickets = [srv.submit(t, d, base.maps, base.lam, base.beta, base.admm_iters, base.cg_iters)
+                   for t, d in reqs]
+        tight = [srv.wait(t)[0] for t in tickets]
+        assert srv.stats()["peak_resident_bytes"] <= one + one // 2
+    with mr.Server(8 << 30, max_inflight=1) as srv:
+        alone = [srv.wait(srv.submit(t, d, base.maps, base.lam, base.beta, base.admm_iters, base.cg_iters))[0]
+                 for t, d in reqs]
+    for a, b in zip(tight, alone):
+        assert np.all(np.isfinite(a)) and np.array_equal(a, b)
+    assert not np.array_equal(alone[0], alone[1])  # the trajectories do differ
