@@ -356,9 +356,27 @@ MRI_API int mri_plan_set_clusters(mri_plan *plan, int fwd_cluster, int adj_clust
 MRI_API int mri_plan_set_graphs(mri_plan *plan, int enable);
 
 /* Autotuner: time every valid cluster size of both products on this plan's
- * shape (`repeats` launches each, default 3) and keep the fastest.
- * Synchronises `stream`; allocates a temporary buffer.  No-op for FP32 plans. */
+ * shape (`repeats` launches each, default 3) and keep the fastest.  The
+ * choice is also recorded in the process-wide tuning table (below), keyed by
+ * precision, shape and SM count.  Synchronises `stream`; allocates a
+ * temporary buffer.  No-op for FP32 plans. */
 MRI_API int mri_plan_autotune(mri_plan *plan, int repeats, mri_stream_t stream);
+
+/* Persistent tuning table.  Plans created for a (precision, nx, ny, nk, nc,
+ * SM count) that the table holds start with its cluster sizes.
+ *   mri_tuning_save: write the table to `path` as JSON
+ *     {"format": "mrirecon-tuning", "version": 1, "entries": [{"precision",
+ *      "nx", "ny", "nk", "nc", "sms", "fwd_cluster", "adj_cluster"}, ...]}
+ *   mri_tuning_load: merge such a file into the table (MRI_ERR_INVALID, and
+ *     no change, for a file that is missing, not a tuning file, or has an
+ *     entry without one of those integer keys or with a cluster size other
+ *     than 1, 2, 4, 8)
+ *   mri_tuning_clear / mri_tuning_count: empty the table / its entry count.
+ * No GPU is needed; the table is guarded for use from several threads. */
+MRI_API int mri_tuning_save(const char *path);
+MRI_API int mri_tuning_load(const char *path);
+MRI_API int mri_tuning_clear(void);
+MRI_API int mri_tuning_count(void);
 
 #ifdef __cplusplus
 }

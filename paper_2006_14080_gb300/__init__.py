@@ -116,6 +116,10 @@ def load(path: str = LIB_PATH):
         "mri_server_stats": ([P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(ctypes.c_uint64),
                               ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Z), ctypes.POINTER(Z)], I),
         "mri_server_destroy": ([P], I),
+        "mri_tuning_save": ([ctypes.c_char_p], I),
+        "mri_tuning_load": ([ctypes.c_char_p], I),
+        "mri_tuning_clear": ([], I),
+        "mri_tuning_count": ([], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -467,3 +471,21 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def tuning_save(path: str):
+    """Write the autotuning table (``mri_tuning_save``)."""
+    _check(load().mri_tuning_save(os.fsencode(path)))
+
+
+def tuning_load(path: str):
+    """Merge a saved autotuning table (``mri_tuning_load``)."""
+    _check(load().mri_tuning_load(os.fsencode(path)))
+
+
+def tuning_clear():
+    _check(load().mri_tuning_clear())
+
+
+def tuning_count() -> int:
+    return int(load().mri_tuning_count())

@@ -299,6 +299,10 @@ int plan_create(mri_plan **out, int nx, int ny, int nk, int nc, const float *tra
     if (e == cudaSuccess) e = cudaMemsetAsync(p->scal, 0, sizeof(DevScalars), s);
     if (e == cudaSuccess && is_tc_precision(precision)) {
         rc = tc_make_tensor_maps(p);
+        int fc = 0, ac = 0;
+        // cluster sizes an earlier autotune chose for this shape, if valid here
+        if (rc == MRI_OK && tuning_lookup(p, &fc, &ac) && tc_cluster_valid_fwd(p, fc) && tc_cluster_valid_adj(p, ac))
+            rc = tc_set_clusters(p, fc, ac);
         if (rc != MRI_OK) {
             free_plan(p);
             return rc;
@@ -669,6 +673,7 @@ MRI_API int mri_plan_autotune(mri_plan *p, int repeats, mri_stream_t stream) {
         }
     }
     if (rc == MRI_OK) rc = tc_set_clusters(p, best_f, best_a);
+    if (rc == MRI_OK) tuning_record(p);
     p->timing = was_timing;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

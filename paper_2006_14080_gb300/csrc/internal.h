@@ -146,6 +146,10 @@ int plan_create(mri_plan **out, int nx, int ny, int nk, int nc, const float *tra
 void plan_destroy_async(mri_plan *p, cudaStream_t s);
 // Drop the cached reconstruction graph (its kernels' arguments are stale).
 void invalidate_graph(mri_plan *p);
+// Persistent autotuning table (tuning.cu): record a plan's cluster sizes /
+// look up the sizes recorded for its precision, shape and SM count.
+void tuning_record(const mri_plan *p);
+bool tuning_lookup(const mri_plan *p, int *fwd_cluster, int *adj_cluster);
 // Argument checks of mri_admm_reconstruct (MRI_* status, sets the error text).
 int check_admm_args(const mri_plan *p, const mri_c64 *kspace, const mri_c64 *maps, const mri_admm_params *prm,
                     const mri_c64 *image_out);

@@ -56,3 +56,40 @@ def test_host_side_validation(lib):
     assert lib.mri_soft_threshold(-1, 0.5, None, None, None) == -1
     assert lib.mri_plan_destroy(None) == 0
     assert lib.mri_plan_device_bytes(None) == 0
+
+
+def test_tuning_table_round_trip(lib, tmp_path):
+    import paper_2006_14080_gb300 as mr
+    src = tmp_path / "tuned.json"
+    src.write_text('{"format": "mrirecon-tuning", "version": 1, "entries": [\n'
+                   ' {"precision": 2, "nx": 128, "ny": 128, "nk": 16384, "nc": 12, "sms": 152,'
+                   ' "fwd_cluster": 4, "adj_cluster": 1},\n'
+                   ' {"precision": 1, "nx": 256, "ny": 256, "nk": 65536, "nc": 32, "sms": 152,'
+                   ' "fwd_cluster": 1, "adj_cluster": 2}\n]}\n')
+    mr.tuning_clear()
+    assert mr.tuning_count() == 0
+    mr.tuning_load(str(src))
+    assert mr.tuning_count() == 2
+    out = tmp_path / "saved.json"
+    mr.tuning_save(str(out))
+    mr.tuning_clear()
+    mr.tuning_load(str(out))
+    assert mr.tuning_count() == 2
+    again = tmp_path / "again.json"
+    mr.tuning_save(str(again))
+    assert again.read_text() == out.read_text()
+    # malformed files are rejected without touching the table
+    bad = [('{"format": "other"}', "not a tuning file"),
+           ('{"format": "mrirecon-tuning", "entries": [{"precision": 2, "nx": 8}]}', "without integer"),
+           ('{"format": "mrirecon-tuning", "entries": [{"precision": 2, "nx": 8, "ny": 8, "nk": 8, "nc": 1,'
+            ' "sms": 152, "fwd_cluster": 3, "adj_cluster": 1}]}', "cluster size")]
+    for text, why in bad:
+        f = tmp_path / "bad.json"
+        f.write_text(text)
+        with pytest.raises(mr.MriError) as ei:
+            mr.tuning_load(str(f))
+        assert ei.value.code == mr.MRI_ERR_INVALID and why in str(ei.value)
+        assert mr.tuning_count() == 2
+    with pytest.raises(mr.MriError):
+        mr.tuning_load(str(tmp_path / "missing.json"))
+    mr.tuning_clear()

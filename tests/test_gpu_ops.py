@@ -191,3 +191,26 @@ def test_invalid_arguments_are_rejected(mr):
                                 torch.zeros((1, 8, 8), dtype=torch.complex64, device="cuda"),
                                 lam=1e-3, beta=0.0, admm_iters=1, cg_iters=1)
         assert ei.value.code == mr.MRI_ERR_INVALID
+
+
+def test_tuning_table_sets_new_plans(mr, tmp_path):
+    # a plan created for a shape the tuning table holds starts with its cluster
+    # sizes; autotune records its choice for the next plan of the same shape
+    nx, ny, nc = 128, 128, 12
+    maps, traj, x, y = _case(nx, ny, nc, 24, 256, seed=41)
+    t = _dev(traj, torch.float32)
+    nk = traj.shape[0]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    f = tmp_path / "t.json"
+    f.write_text('{"format": "mrirecon-tuning", "version": 1, "entries": [{"precision": 2, "nx": %d, "ny": %d, '
+                 '"nk": %d, "nc": %d, "sms": %d, "fwd_cluster": 1, "adj_cluster": 4}]}' % (nx, ny, nk, nc, sms))
+    mr.tuning_clear()
+    mr.tuning_load(str(f))
+    with mr.Plan(nx, ny, nc, t, "bf16x3") as plan:
+        cfg = plan.config()
+        assert (cfg["fwd_cluster"], cfg["adj_cluster"]) == (1, 4)
+        tuned = plan.autotune(repeats=2)
+    with mr.Plan(nx, ny, nc, t, "bf16x3") as plan:
+        cfg = plan.config()
+        assert (cfg["fwd_cluster"], cfg["adj_cluster"]) == (tuned["fwd_cluster"], tuned["adj_cluster"])
+    mr.tuning_clear()
