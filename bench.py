@@ -66,6 +66,24 @@ def captured_traffic(kernel: str, workload: str):
     return entry[0], entry[2]
 
 
+def max_over_ranks_fn(dist, device):
+    """The maximum over ranks of a host number (the slowest rank's clock); the
+    identity without a process group."""
+    def reduce_max(v: float) -> float:
+        if dist is None:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return reduce_max
+
+
+def whole_job_rate(units_per_rank: float, slowest_ms: float, world: int) -> float:
+    """Units all ranks processed per second of the slowest rank."""
+    return world * units_per_rank / (slowest_ms / 1e3)
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -184,12 +202,7 @@ def run_gpu(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = max_over_ranks_fn(dist, dev)
 
     def timed_steps(plan, out, steps, warmup, host=None, plan_timed=False):
         """Returns (per-step device ms list, launches per step)."""
@@ -288,7 +301,7 @@ def run_gpu(args, rank, world, local_rank):
     t32_ms = max_over_ranks(sum(t32))
     if rank != 0:
         return None
-    recon_s = world * args.steps / (total_ms / 1e3)
+    recon_s = whole_job_rate(args.steps, total_ms, world)
     flops_prod = useful_flops_per_product(p)
     pk, pk_kind = peaks()
     # dominant kernel: the product kernel with the larger share of the timed region
@@ -326,7 +339,7 @@ def run_gpu(args, rank, world, local_rank):
                    "readout": p.readout, "admm_iters": p.admm_iters, "cg_iters": p.cg_iters, "lambda": p.lam,
                    "beta": p.beta, "l2": "flushed (512 MB write) between timed steps",
                    "step": "factor generation for the step's trajectory + full ADMM reconstruction"},
-        "e2e": {"value": world * args.steps / (e2e_ms / 1e3), "unit": "recon/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": whole_job_rate(args.steps, e2e_ms, world), "unit": "recon/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "tuning": tuned,
@@ -345,7 +358,7 @@ def run_gpu(args, rank, world, local_rank):
                   "reduce_share_of_step": timing["red_ms"] / kernel_pass_ms,
                   "direct_launch_ms_per_step": kernel_pass_ms / len(ktimes),
                   "recon_useful_tflops": useful_tflops_step},
-        "fp32_form": {"value": world * fp32_steps / (t32_ms / 1e3), "unit": "recon/s",
+        "fp32_form": {"value": whole_job_rate(fp32_steps, t32_ms, world), "unit": "recon/s",
                       "ms_per_step": t32_ms / fp32_steps, "gpu_launches": l32,
                       "fwd_ms_per_launch": timing32["fwd_ms"] / max(1, timing32["fwd_launches"]),
                       "adj_ms_per_launch": timing32["adj_ms"] / max(1, timing32["adj_launches"])},
@@ -362,7 +375,7 @@ def run_gpu(args, rank, world, local_rank):
         # measured BF16 peak x the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
         tf32_peak = peak_tf * 1.1 / 2.25
         line["tf32_form"] = {
-            "value": world * args.steps / (tt_ms / 1e3), "unit": "recon/s", "ms_per_step": tt_ms / args.steps,
+            "value": whole_job_rate(args.steps, tt_ms, world), "unit": "recon/s", "ms_per_step": tt_ms / args.steps,
             "gpu_launches": lt_, "tuning": tuned_t, "fwd_ms_per_launch": f_avg, "adj_ms_per_launch": a_avg,
             "fwd_tflops": flops_prod / (f_avg * 1e-3) / 1e12, "adj_tflops": flops_prod / (a_avg * 1e-3) / 1e12,
             "peak_tflops": tf32_peak, "peak_note": f"{pk_kind} sustained bf16 x 1.1/2.25 (nominal TF32/BF16)",
@@ -426,11 +439,7 @@ def run_batch(args, rank, world, local_rank):
         batch.reconstruct(items)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks_fn(dist, dev)(sum(a.elapsed_time(b) for a, b in ev))
     launches = batch.launch_count()
     batch.close()
     for pl in plans:
@@ -441,7 +450,7 @@ def run_batch(args, rank, world, local_rank):
     return {
         "metric": f"ADMM recon/s, batch of {n} heterogeneous reconstructions (N 64-256, 8-32 coils, 32-200 "
                   f"golden-angle spokes x 2N, 30 ADMM x 8 CG), BF16x3, one batched graph launch per step",
-        "value": world * n * args.steps / (total_ms / 1e3), "unit": "recon/s", "n_gpus": world,
+        "value": whole_job_rate(n * args.steps, total_ms, world), "unit": "recon/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3/f32",
         "data": "synthetic (seeded per item)",

@@ -325,6 +325,7 @@ extern "C" {
 
 MRI_API int mri_plan_create(mri_plan **out, int nx, int ny, int nk, int nc, const float *traj, int precision,
                             mri_stream_t stream) {
+    NvtxRange range("mri_plan_create");
     return plan_create(out, nx, ny, nk, nc, traj, precision, (cudaStream_t)stream, nullptr);
 }
 
@@ -398,6 +399,7 @@ MRI_API size_t mri_plan_estimate_bytes(int nx, int ny, int nk, int nc, int preci
 
 MRI_API int mri_nudft_forward(mri_plan *p, const mri_c64 *image, const mri_c64 *maps, mri_c64 *kspace,
                               mri_stream_t stream) {
+    NvtxRange range("mri_nudft_forward");
     if (!p || !image || !maps || !kspace) return fail(MRI_ERR_INVALID, "null argument");
     cudaError_t e = op_forward(p, (const float2 *)image, (const float2 *)maps, (float2 *)kspace, p->nk, kSkipNever,
                                (cudaStream_t)stream);
@@ -407,6 +409,7 @@ MRI_API int mri_nudft_forward(mri_plan *p, const mri_c64 *image, const mri_c64 *
 
 MRI_API int mri_nudft_adjoint(mri_plan *p, const mri_c64 *kspace, const mri_c64 *maps, mri_c64 *image,
                               mri_stream_t stream) {
+    NvtxRange range("mri_nudft_adjoint");
     if (!p || !image || !maps || !kspace) return fail(MRI_ERR_INVALID, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = op_adjoint_partials(p, (const float2 *)kspace, kSkipNever, s);
@@ -417,6 +420,7 @@ MRI_API int mri_nudft_adjoint(mri_plan *p, const mri_c64 *kspace, const mri_c64 
 
 MRI_API int mri_normal_op(mri_plan *p, const mri_c64 *image, const mri_c64 *maps, float beta, mri_c64 *out,
                           mri_stream_t stream) {
+    NvtxRange range("mri_normal_op");
     if (!p || !image || !maps || !out) return fail(MRI_ERR_INVALID, "null argument");
     if (!finite(beta) || beta < 0.f) return fail(MRI_ERR_INVALID, "beta must be finite and >= 0");
     if ((const void *)image == (const void *)out) return fail(MRI_ERR_INVALID, "image and out must differ");
@@ -515,6 +519,7 @@ extern "C" {
 MRI_API int mri_admm_reconstruct(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in,
                                  const mri_admm_params *prm, mri_c64 *image_out, double *objective_hist,
                                  double *alpha_hist, mri_stream_t stream) {
+    NvtxRange range("mri_admm_reconstruct");
     const int arc = check_admm_args(p, kspace_in, maps_in, prm, image_out);
     if (arc != MRI_OK) return arc;
     cudaStream_t s = (cudaStream_t)stream;

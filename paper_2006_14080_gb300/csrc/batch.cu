@@ -73,6 +73,7 @@ MRI_API int mri_batch_destroy(mri_batch *b) {
 MRI_API long long mri_batch_launch_count(const mri_batch *b) { return b ? b->launches : 0; }
 
 MRI_API int mri_batch_reconstruct(mri_batch *b, int n, const mri_request *reqs, mri_stream_t stream) {
+    NvtxRange range("mri_batch_reconstruct");
     if (!b || n <= 0 || !reqs) return fail(MRI_ERR_INVALID, "null batch, empty request list or null requests");
     for (int q = 0; q < n; ++q) {
         const mri_request &r = reqs[q];

@@ -12,6 +12,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mrirecon.h"
 
 namespace mri {
@@ -47,6 +49,15 @@ enum Counter : int { kCntDot = 0, kCntTau = 1, kCntInit = 2, kCntDual = 3, kCntO
 // Tile constants of the tensor-core kernels.
 constexpr int kTcBlockM = 128;   // UMMA M (rows of the real-embedded operand)
 constexpr int kTcBlockK = 64;    // bf16 elements per 128-byte swizzled row
+
+// Host-side NVTX range around a library call (shown on Nsight timelines; ncu
+// can select the kernels a call launched with --nvtx --nvtx-include).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 inline bool is_tc_precision(int precision) { return precision == MRI_BF16X3 || precision == MRI_TF32; }
 

@@ -126,6 +126,7 @@ void fail_job(mri_server *s, Job *j, int code, const std::string &msg) {
 
 // Starts a job on its slot (called by the worker with the lock held).
 int start_job(mri_server *s, Job *j) {
+    mri::NvtxRange range("mri_server_start_job");
     cudaStream_t st = s->streams[j->slot];
     const mri_server_request &r = j->req;
     cudaError_t e = cudaSuccess;
