@@ -84,6 +84,43 @@ def whole_job_rate(units_per_rank: float, slowest_ms: float, world: int) -> floa
     return world * units_per_rank / (slowest_ms / 1e3)
 
 
+def gemm_peak_tflops(tf32: bool, seconds: float = 3.0, n: int = 8192):
+    """cuBLAS FP32 GEMM throughput on this GPU (TF32 tensor cores when tf32,
+    else the FFMA path): (best of 10 single calls, mean over a back-to-back
+    loop of `seconds`), in TFLOP/s; the denominators of the TF32 and FP32
+    forms, which MEASURED_PEAKS.json does not carry."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = tf32
+    try:
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        c = torch.empty(n, n, device="cuda")
+        flops = 2.0 * n ** 3
+        for _ in range(3):
+            torch.matmul(a, b, out=c)
+        best = float("inf")
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        reps = max(1, int(seconds * 1e3 / best))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(a, b, out=c)
+        e1.record()
+        e1.synchronize()
+        sustained = reps * flops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        del a, b, c
+        return flops / (best * 1e-3) / 1e12, sustained
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -294,6 +331,13 @@ def run_gpu(args, rank, world, local_rank):
             timing_t = plan_t.read_timing()
         tf32 = (tt, lt_, timing_t, tuned_t, x_tf32)
 
+    # denominators of the TF32 and FP32 forms (cuBLAS GEMMs, outside every timed region)
+    gemm_peaks = {}
+    for name, on in (("tf32", True), ("fp32", False)):
+        if name in forms:
+            burst, sustained = gemm_peak_tflops(on)
+            gemm_peaks[name] = {"burst": burst, "sustained": sustained}
+
     # ---------------------------------------------------------------- report
     times, launches, timing, clocks = results["bf16x3"]
     total_ms = max_over_ranks(sum(times))
@@ -362,6 +406,7 @@ def run_gpu(args, rank, world, local_rank):
                       "ms_per_step": t32_ms / fp32_steps, "gpu_launches": l32,
                       "fwd_ms_per_launch": timing32["fwd_ms"] / max(1, timing32["fwd_launches"]),
                       "adj_ms_per_launch": timing32["adj_ms"] / max(1, timing32["adj_launches"])},
+        "gemm_peaks_tflops": gemm_peaks,
         "tf32_form": None,
         "nrmse_vs_fp64_oracle": nrmse_vs_golden,
         "clocks": clocks,
@@ -372,16 +417,29 @@ def run_gpu(args, rank, world, local_rank):
         f_avg = timing_t["fwd_ms"] / max(1, timing_t["fwd_launches"])
         a_avg = timing_t["adj_ms"] / max(1, timing_t["adj_launches"])
         # one TF32 product executes the useful flops once; TF32 dense peak =
+        # the cuBLAS TF32 GEMM measured in this run (sustained), else the
         # measured BF16 peak x the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
-        tf32_peak = peak_tf * 1.1 / 2.25
+        if "tf32" in gemm_peaks:
+            tf32_peak, tf32_note = gemm_peaks["tf32"]["sustained"], "cuBLAS TF32 GEMM 8192^3, measured in this run"
+        else:
+            tf32_peak, tf32_note = peak_tf * 1.1 / 2.25, f"{pk_kind} sustained bf16 x 1.1/2.25 (nominal TF32/BF16)"
         line["tf32_form"] = {
             "value": whole_job_rate(args.steps, tt_ms, world), "unit": "recon/s", "ms_per_step": tt_ms / args.steps,
             "gpu_launches": lt_, "tuning": tuned_t, "fwd_ms_per_launch": f_avg, "adj_ms_per_launch": a_avg,
             "fwd_tflops": flops_prod / (f_avg * 1e-3) / 1e12, "adj_tflops": flops_prod / (a_avg * 1e-3) / 1e12,
-            "peak_tflops": tf32_peak, "peak_note": f"{pk_kind} sustained bf16 x 1.1/2.25 (nominal TF32/BF16)",
+            "peak_tflops": tf32_peak, "peak_note": tf32_note,
             "adj_frac": flops_prod / (a_avg * 1e-3) / 1e12 / tf32_peak,
             "fwd_frac": flops_prod / (f_avg * 1e-3) / 1e12 / tf32_peak,
         }
+    if line["fp32_form"] is not None and "fp32" in gemm_peaks:
+        f32 = line["fp32_form"]
+        pk32 = gemm_peaks["fp32"]["sustained"]
+        f32.update({"fwd_tflops": flops_prod / (f32["fwd_ms_per_launch"] * 1e-3) / 1e12,
+                    "adj_tflops": flops_prod / (f32["adj_ms_per_launch"] * 1e-3) / 1e12,
+                    "peak_tflops": pk32, "peak_note": "cuBLAS FP32 GEMM (FFMA, TF32 off) 8192^3, measured in this run"})
+        f32["adj_frac"] = f32["adj_tflops"] / pk32
+        f32["fwd_frac"] = f32["fwd_tflops"] / pk32
+    if tf32 is not None:
         if nrmse_vs_golden is not None:
             xg = np.load(gpath)["x"]
             nrmse_vs_golden["tf32"] = float(np.linalg.norm(x_tf32 - xg) / np.linalg.norm(xg))

@@ -179,6 +179,23 @@ MRI_API int mri_admm_reconstruct(mri_plan *plan, const mri_c64 *kspace, const mr
                                  const mri_admm_params *params, mri_c64 *image_out,
                                  double *objective_hist, double *alpha_hist, mri_stream_t stream);
 
+/*
+ * Checkpoint and resume (not in the paper): Alg. 4 started from a saved state
+ * instead of x^0 = 0, eta^0 = 0.  x0 [nx][ny] and eta0 [2][nx][ny] (device,
+ * nullable: zero) are the image and the dual variable to start from; on
+ * return image_out holds x and eta_out ([2][nx][ny], nullable) the dual
+ * variable, which must not alias x0 or eta0.  The ADMM state is exactly
+ * (x, eta) -- mu is recomputed from them at the start of each step -- so with
+ * fixed counts (rtol = atol = 0) a reconstruction split into two calls, the
+ * second resuming from the first one's (x, eta), computes bit for bit the
+ * iterates of one call with the summed admm_iters.  objective_hist and
+ * alpha_hist count the steps of this call.
+ */
+MRI_API int mri_admm_resume(mri_plan *plan, const mri_c64 *kspace, const mri_c64 *coil_maps,
+                            const mri_admm_params *params, const mri_c64 *x0, const mri_c64 *eta0,
+                            mri_c64 *image_out, mri_c64 *eta_out, double *objective_hist, double *alpha_hist,
+                            mri_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Batched reconstructions (not in the paper, which reconstructs one image
  * at a time): many independent problems of different shapes in one launch.

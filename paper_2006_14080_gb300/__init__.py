@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
         "mri_tv_adjoint": ([I, I, P, P, P], I),
         "mri_soft_threshold": ([I, F, P, P, P], I),
         "mri_admm_reconstruct": ([P, P, P, ctypes.POINTER(AdmmParams), P, P, P, P], I),
+        "mri_admm_resume": ([P, P, P, ctypes.POINTER(AdmmParams), P, P, P, P, P, P, P], I),
         "mri_nudft_adjoint_noalloc": ([I, I, I, I, P, P, P, P, P], I),
         "mri_plan_set_timing": ([P, I], I),
         "mri_plan_read_timing": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
@@ -334,6 +335,34 @@ def admm_reconstruct(plan: Plan, kspace, coil_maps, lam: float, beta: float, adm
     _check(load().mri_admm_reconstruct(plan.handle, _ptr(kspace), _ptr(coil_maps), ctypes.byref(prm), _ptr(out),
                                        _ptr(objective_hist), _ptr(alpha_hist), _stream(stream)))
     return out
+
+
+def admm_resume(plan: Plan, kspace, coil_maps, lam: float, beta: float, admm_iters: int, cg_iters: int,
+                x0=None, eta0=None, rtol: float = 0.0, atol: float = 0.0, out=None, eta_out=None,
+                objective_hist=None, alpha_hist=None, stream=None):
+    """Alg. 4 from a saved state (``mri_admm_resume``): ``x0`` ``[nx, ny]`` and
+    ``eta0`` ``[2, nx, ny]`` (None: zero).  Returns ``(image, eta)``; ``eta`` is
+    a new tensor unless ``eta_out`` is given."""
+    _need(kspace, torch.complex64, (plan.nc, plan.nk), "kspace")
+    _need(coil_maps, torch.complex64, (plan.nc, plan.nx, plan.ny), "coil_maps")
+    if x0 is not None:
+        _need(x0, torch.complex64, (plan.nx, plan.ny), "x0")
+    if eta0 is not None:
+        _need(eta0, torch.complex64, (2, plan.nx, plan.ny), "eta0")
+    if out is None:
+        out = torch.empty((plan.nx, plan.ny), dtype=torch.complex64, device=kspace.device)
+    if eta_out is None:
+        eta_out = torch.empty((2, plan.nx, plan.ny), dtype=torch.complex64, device=kspace.device)
+    _need(out, torch.complex64, (plan.nx, plan.ny), "image_out")
+    _need(eta_out, torch.complex64, (2, plan.nx, plan.ny), "eta_out")
+    for h, name in ((objective_hist, "objective_hist"), (alpha_hist, "alpha_hist")):
+        if h is not None:
+            _need(h, torch.float64, (admm_iters,), name)
+    prm = AdmmParams(float(lam), float(beta), int(admm_iters), int(cg_iters), float(rtol), float(atol))
+    _check(load().mri_admm_resume(plan.handle, _ptr(kspace), _ptr(coil_maps), ctypes.byref(prm), _ptr(x0),
+                                  _ptr(eta0), _ptr(out), _ptr(eta_out), _ptr(objective_hist), _ptr(alpha_hist),
+                                  _stream(stream)))
+    return out, eta_out
 
 
 class Batch:

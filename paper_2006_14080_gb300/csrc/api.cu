@@ -456,7 +456,8 @@ MRI_API int mri_soft_threshold(int n, float t, const mri_c64 *in, mri_c64 *out, 
 
 // Enqueue the whole reconstruction (Alg. 4 with Alg. 2) on s.
 int mri::enqueue_admm(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in, const mri_admm_params *prm,
-                      mri_c64 *image_out, double *objective_hist, double *alpha_hist, cudaStream_t s) {
+                      mri_c64 *image_out, double *objective_hist, double *alpha_hist, cudaStream_t s,
+                      const AdmmWarm &warm) {
     const float2 *kspace = (const float2 *)kspace_in;
     const float2 *maps = (const float2 *)maps_in;
     const size_t npix = (size_t)p->nx * p->ny;
@@ -475,8 +476,15 @@ int mri::enqueue_admm(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps
     } while (0)
 
     KERNEL(launch_admm_reset(p, prm->atol, prm->rtol, s));
-    STEP(cudaMemsetAsync(p->x, 0, npix * sizeof(float2), s));
-    STEP(cudaMemsetAsync(p->eta, 0, 2 * npix * sizeof(float2), s));
+    // x^0 = 0 and eta^0 = 0 (Alg. 4), or a saved state to resume from
+    if (warm.x0)
+        STEP(cudaMemcpyAsync(p->x, warm.x0, npix * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    else
+        STEP(cudaMemsetAsync(p->x, 0, npix * sizeof(float2), s));
+    if (warm.eta0)
+        STEP(cudaMemcpyAsync(p->eta, warm.eta0, 2 * npix * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    else
+        STEP(cudaMemsetAsync(p->eta, 0, 2 * npix * sizeof(float2), s));
     // F^H d, once per reconstruction (Section IV-C: the right-hand side stays
     // fixed through the CG iterations)
     STEP(op_adjoint_partials(p, kspace, kSkipNever, s));
@@ -498,6 +506,8 @@ int mri::enqueue_admm(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps
         }
     }
     STEP(cudaMemcpyAsync(image_out, p->x, npix * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    if (warm.eta_out)
+        STEP(cudaMemcpyAsync(warm.eta_out, p->eta, 2 * npix * sizeof(float2), cudaMemcpyDeviceToDevice, s));
 #undef KERNEL
 #undef STEP
     return MRI_OK;
@@ -516,19 +526,22 @@ int mri::check_admm_args(const mri_plan *p, const mri_c64 *kspace_in, const mri_
 
 extern "C" {
 
-MRI_API int mri_admm_reconstruct(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in,
-                                 const mri_admm_params *prm, mri_c64 *image_out, double *objective_hist,
-                                 double *alpha_hist, mri_stream_t stream) {
-    NvtxRange range("mri_admm_reconstruct");
+}  // extern "C"
+
+// mri_admm_reconstruct and mri_admm_resume: direct launches, or the cached
+// CUDA graph of the whole reconstruction while the arguments repeat.
+static int admm_run(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in, const mri_admm_params *prm,
+                    mri_c64 *image_out, double *objective_hist, double *alpha_hist, const AdmmWarm &warm,
+                    cudaStream_t s) {
     const int arc = check_admm_args(p, kspace_in, maps_in, prm, image_out);
     if (arc != MRI_OK) return arc;
-    cudaStream_t s = (cudaStream_t)stream;
     // per-kernel timing events cannot be read back from graph replays, so a
     // timed plan launches its kernels directly
     if (!p->use_graphs || s == nullptr || p->timing)
-        return enqueue_admm(p, kspace_in, maps_in, prm, image_out, objective_hist, alpha_hist, s);
-    const mri_plan::GraphKey key{kspace_in, maps_in,         image_out,     objective_hist, alpha_hist,
-                                 prm->lambda, prm->beta, prm->admm_iters, prm->cg_iters, prm->rtol, prm->atol};
+        return enqueue_admm(p, kspace_in, maps_in, prm, image_out, objective_hist, alpha_hist, s, warm);
+    const mri_plan::GraphKey key{kspace_in,  maps_in,   image_out,       objective_hist, alpha_hist,
+                                 prm->lambda, prm->beta, prm->admm_iters, prm->cg_iters,  prm->rtol,
+                                 prm->atol,   warm.x0,   warm.eta0,       warm.eta_out};
     if (p->graph_exec && p->graph_key == key) {
         cudaError_t e = cudaGraphLaunch(p->graph_exec, s);
         if (e != cudaSuccess) return cuda_fail(e, "graph launch");
@@ -539,7 +552,7 @@ MRI_API int mri_admm_reconstruct(mri_plan *p, const mri_c64 *kspace_in, const mr
     const long long l0 = p->launches;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "graph capture");
-    const int rc = enqueue_admm(p, kspace_in, maps_in, prm, image_out, objective_hist, alpha_hist, s);
+    const int rc = enqueue_admm(p, kspace_in, maps_in, prm, image_out, objective_hist, alpha_hist, s, warm);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(s, &graph);
     if (rc != MRI_OK || e != cudaSuccess) {
@@ -559,6 +572,29 @@ MRI_API int mri_admm_reconstruct(mri_plan *p, const mri_c64 *kspace_in, const mr
     e = cudaGraphLaunch(p->graph_exec, s);
     if (e != cudaSuccess) return cuda_fail(e, "graph launch");
     return MRI_OK;
+}
+
+extern "C" {
+
+MRI_API int mri_admm_reconstruct(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in,
+                                 const mri_admm_params *prm, mri_c64 *image_out, double *objective_hist,
+                                 double *alpha_hist, mri_stream_t stream) {
+    NvtxRange range("mri_admm_reconstruct");
+    return admm_run(p, kspace_in, maps_in, prm, image_out, objective_hist, alpha_hist, AdmmWarm(),
+                    (cudaStream_t)stream);
+}
+
+MRI_API int mri_admm_resume(mri_plan *p, const mri_c64 *kspace, const mri_c64 *maps, const mri_admm_params *prm,
+                            const mri_c64 *x0, const mri_c64 *eta0, mri_c64 *image_out, mri_c64 *eta_out,
+                            double *objective_hist, double *alpha_hist, mri_stream_t stream) {
+    NvtxRange range("mri_admm_resume");
+    AdmmWarm warm;
+    warm.x0 = x0;
+    warm.eta0 = eta0;
+    warm.eta_out = eta_out;
+    if (eta_out && (eta_out == eta0 || (const void *)eta_out == (const void *)x0))
+        return fail(MRI_ERR_INVALID, "eta_out must not alias x0 or eta0");
+    return admm_run(p, kspace, maps, prm, image_out, objective_hist, alpha_hist, warm, (cudaStream_t)stream);
 }
 
 MRI_API int mri_plan_set_graphs(mri_plan *p, int enable) {

@@ -138,10 +138,12 @@ struct mri_plan {
         float lambda, beta;
         int admm_iters, cg_iters;
         double rtol, atol;
+        const void *x0, *eta0, *eta_out;  // resumed reconstructions (else null)
         bool operator==(const GraphKey &o) const {
             return kspace == o.kspace && maps == o.maps && image_out == o.image_out && obj == o.obj &&
                    alpha == o.alpha && lambda == o.lambda && beta == o.beta && admm_iters == o.admm_iters &&
-                   cg_iters == o.cg_iters && rtol == o.rtol && atol == o.atol;
+                   cg_iters == o.cg_iters && rtol == o.rtol && atol == o.atol && x0 == o.x0 && eta0 == o.eta0 &&
+                   eta_out == o.eta_out;
         }
     } graph_key{};
     cudaGraphExec_t graph_exec = nullptr;
@@ -164,9 +166,16 @@ bool tuning_lookup(const mri_plan *p, int *fwd_cluster, int *adj_cluster);
 // Argument checks of mri_admm_reconstruct (MRI_* status, sets the error text).
 int check_admm_args(const mri_plan *p, const mri_c64 *kspace, const mri_c64 *maps, const mri_admm_params *prm,
                     const mri_c64 *image_out);
+// Saved ADMM state to start from (x0, eta0; null = zero) and where to leave
+// the final dual variable (eta_out, nullable).
+struct AdmmWarm {
+    const mri_c64 *x0 = nullptr, *eta0 = nullptr;
+    mri_c64 *eta_out = nullptr;
+};
 // Enqueue one whole reconstruction (Alg. 4 with Alg. 2) on s; MRI_* status.
 int enqueue_admm(mri_plan *p, const mri_c64 *kspace, const mri_c64 *maps, const mri_admm_params *prm,
-                 mri_c64 *image_out, double *objective_hist, double *alpha_hist, cudaStream_t s);
+                 mri_c64 *image_out, double *objective_hist, double *alpha_hist, cudaStream_t s,
+                 const AdmmWarm &warm = AdmmWarm());
 }  // namespace mri
 
 // Record the timing events (when set) immediately around a product kernel.

@@ -56,7 +56,12 @@ constexpr int kAyChunkBytes = 32 * 64 * 8;        // 32 columns x 64 samples, co
 constexpr int kRawBytes = 2 * 64 * 128;           // 64 pixels x 32 samples of A_x^H, complex FP32
 constexpr int kRawYBytes = 32 * 8;                // 32 samples of y_c
 constexpr int kFwdThreads = 224;                  // w0 TMA, w1 UMMA, w2 A_y TMA, w3-6 epilogue
-constexpr int kAdjProducerWarps = 8;              // adjoint: w0-7 producers, w8 UMMA, w9-12 epilogue, w13 TMA
+#ifndef MRI_ADJ_PRODUCER_WARPS
+#define MRI_ADJ_PRODUCER_WARPS 8
+#endif
+// adjoint: producer warps (8 or 16), then the UMMA warp, 4 epilogue warps, the TMA warp
+constexpr int kAdjProducerWarps = MRI_ADJ_PRODUCER_WARPS;
+static_assert(kAdjProducerWarps == 8 || kAdjProducerWarps == 16, "8 or 16 producer warps");
 constexpr int kAdjProducers = 32 * kAdjProducerWarps;
 constexpr int kAdjMmaWarp = kAdjProducerWarps;
 constexpr int kAdjLoaderWarp = kAdjProducerWarps + 5;
@@ -515,11 +520,14 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
 
     if (warp < kAdjProducerWarps) {
         // producers: warp w owns TMEM lanes [32 (w%4), 32 (w%4) + 32) and the
-        // sixteen samples [16 kh, 16 kh + 16) of each K block (kh = w/4).
+        // kSpw samples [kSpw kh, kSpw kh + kSpw) of each K block (kh = w/4).
         // Lane l holds row r = 32 (w%4) + l of U's real embedding: pixel
         // ii = r/2, Re row (o = 0) or Im row (o = 1).  The two threads of a
-        // pixel each form eight of the sixteen products and swap halves.
+        // pixel each form half of the warp's products and swap halves.
+        constexpr int kSpw = 128 / kAdjProducerWarps;  // samples per warp and K block
+        constexpr int kCpt = kSpw / 4;                  // 16-byte chunks (two samples) per thread
         const int q = warp & 3, kh = warp >> 2;
+        const int half = (kSpw * kh) >> 4, chunk0 = ((kSpw * kh) & 15) >> 1;
         const int row = 32 * q + lane;
         const int ii = row >> 1, o = row & 1;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
@@ -554,18 +562,18 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                     issued_phase[rs.stage] = rs.phase;
                     issued_mask |= 1 << rs.stage;
                 }
-                // staged A_x^H half-row kh (128-byte swizzled) and y_c chunk:
-                // this thread's samples are chunks 4o .. 4o+3 of the half
-                const uint8_t *arow = raw + (size_t)rr.stage * kRawBytes + kh * (kRawBytes / 2) + ii * 128;
+                // staged A_x^H half-row (128-byte swizzled, sixteen samples) and
+                // y_c chunk: this thread's samples are chunks chunk0 + kCpt o + c
+                const uint8_t *arow = raw + (size_t)rr.stage * kRawBytes + half * (kRawBytes / 2) + ii * 128;
                 const float4 *yv4 =
-                    reinterpret_cast<const float4 *>(yraw + (size_t)rr.stage * kRawYBytes + kh * 128);
-                const uint32_t acol = (uint32_t)(P.a_col0 + 64 * rs.stage + (kTf32 ? 32 : 16) * kh);
+                    reinterpret_cast<const float4 *>(yraw + (size_t)rr.stage * kRawYBytes + half * 128);
+                const uint32_t acol = (uint32_t)(P.a_col0 + 64 * rs.stage + (kTf32 ? 2 * kSpw : kSpw) * kh);
                 if constexpr (kTf32) {
-                    // this thread's eight samples: Re-row pairs (ur, -ui) and Im-row pairs (ui, ur)
-                    uint32_t rw[16], iw[16];
+                    // this thread's 2 kCpt samples: Re-row pairs (ur, -ui) and Im-row pairs (ui, ur)
+                    uint32_t rw[4 * kCpt], iw[4 * kCpt];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int chunk = 4 * o + c;
+                    for (int c = 0; c < kCpt; ++c) {
+                        const int chunk = chunk0 + kCpt * o + c;
                         const float4 av = *reinterpret_cast<const float4 *>(arow + ((chunk ^ (ii & 7)) << 4));
                         const float4 yv = yv4[chunk];
                         const float2 u0 = cmulc(make_float2(av.x, av.y), make_float2(yv.x, yv.y));
@@ -585,19 +593,19 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                     rr.next(R);
                     // the Re-row thread (o = 0) keeps its Re pairs and receives the
                     // partner's; the Im-row thread likewise, in sample order
-                    uint32_t w[32];
+                    uint32_t w[2 * kSpw];
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) {
+                    for (int e = 0; e < 4 * kCpt; ++e) {
                         const uint32_t rcv = __shfl_xor_sync(0xffffffffu, o ? rw[e] : iw[e], 1);
                         w[e] = o ? rcv : rw[e];
-                        w[16 + e] = o ? iw[e] : rcv;
+                        w[4 * kCpt + e] = o ? iw[e] : rcv;
                     }
-                    tmem_st_32cols(tmem_base + lane_base + acol, w);
+                    tmem_st_cols<2 * kSpw>(tmem_base + lane_base + acol, w);
                 } else {
-                    uint32_t hre[8], lre[8], him[8], lim[8];
+                    uint32_t hre[2 * kCpt], lre[2 * kCpt], him[2 * kCpt], lim[2 * kCpt];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int chunk = 4 * o + c;
+                    for (int c = 0; c < kCpt; ++c) {
+                        const int chunk = chunk0 + kCpt * o + c;
                         const float4 av = *reinterpret_cast<const float4 *>(arow + ((chunk ^ (ii & 7)) << 4));
                         const float4 yv = yv4[chunk];
                         split_embed(cmulc(make_float2(av.x, av.y), make_float2(yv.x, yv.y)), hre[2 * c],
@@ -609,18 +617,18 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                     rr.next(R);
                     // the Re-row thread keeps its Re words and receives the
                     // partner's; the Im-row thread likewise, in sample order
-                    uint32_t hi[16], lo[16];
+                    uint32_t hi[kSpw], lo[kSpw];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
+                    for (int e = 0; e < 2 * kCpt; ++e) {
                         const uint32_t rh = __shfl_xor_sync(0xffffffffu, o ? hre[e] : him[e], 1);
                         const uint32_t rl = __shfl_xor_sync(0xffffffffu, o ? lre[e] : lim[e], 1);
                         hi[e] = o ? rh : hre[e];
                         lo[e] = o ? rl : lre[e];
-                        hi[8 + e] = o ? him[e] : rh;
-                        lo[8 + e] = o ? lim[e] : rl;
+                        hi[2 * kCpt + e] = o ? him[e] : rh;
+                        lo[2 * kCpt + e] = o ? lim[e] : rl;
                     }
-                    tmem_st_16cols(tmem_base + lane_base + acol, hi);
-                    tmem_st_16cols(tmem_base + lane_base + acol + 32, lo);
+                    tmem_st_cols<kSpw>(tmem_base + lane_base + acol, hi);
+                    tmem_st_cols<kSpw>(tmem_base + lane_base + acol + 32, lo);
                 }
                 tmem_wait_st();
                 fence_before_sync();

@@ -42,47 +42,63 @@ __device__ __forceinline__ float2 theta_h_theta_at(const float2 *p, int i, int j
 }
 
 // out[i][j] = sum_c conj(S_c[i][j]) sum_p part[p][c][j][i]  (+ half_beta Theta^H Theta tv_src)
-// and optionally Re<dot_src, out> -> alpha = tau / dot.  Block (32, 16)
-// covers 32 consecutive pixels i of one column j; thread row ty takes the
-// coils c = ty, ty + 16, ..., sums each coil's k-space splits (reads
-// coalesced along i, four in flight, combined in a fixed order), applies
-// conj(S_c) once per coil, and the sixteen groups are added in a fixed order.
+// and optionally Re<dot_src, out> -> alpha = tau / dot.  Block (32, G),
+// G = min(nc, 16): it covers 32 consecutive pixels i of the column pair
+// (j0, j0 + 1); thread row ty takes the coils c = ty, ty + G, ..., sums each
+// coil's k-space splits for both columns (reads coalesced along i, eight in
+// flight, combined in a fixed order), applies conj(S_c) once per coil and
+// pixel, and the G groups are added in a fixed order.  Two columns per block
+// halve the grid so that it fits the GPU in one wave at the common sizes.
 constexpr int kReduceGroups = 16;
-__global__ void __launch_bounds__(32 * kReduceGroups)
+__global__ void __launch_bounds__(32 * kReduceGroups, 2)
     adj_reduce_kernel(const float2 *__restrict__ part, int ksplit, int nc, int nx, int ny, int nx_pad,
                       const float2 *__restrict__ maps, float2 *__restrict__ out, const float2 *__restrict__ tv_src,
                       float half_beta, const float2 *__restrict__ dot_src, DevScalars *sc, double *partials,
                       int skip) {
     if (should_skip(sc, skip)) return;
-    __shared__ float2 grp[kReduceGroups][32];
+    __shared__ float2 grp[kReduceGroups][2][32];
     __shared__ double red[32];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i = blockIdx.x * 32 + tx, j = blockIdx.y;
+    const int tx = threadIdx.x, ty = threadIdx.y, G = blockDim.y;
+    const int i = blockIdx.x * 32 + tx, j0 = blockIdx.y * 2;
+    const bool has1 = j0 + 1 < ny;
     const size_t npix = (size_t)nx * ny;
-    float2 acc = make_float2(0.f, 0.f);
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
     if (i < nx) {
         const size_t pstride = (size_t)nc * ny * nx_pad;  // between k-space splits
-        for (int c = ty; c < nc; c += kReduceGroups) {
-            const float2 *src = part + ((size_t)c * ny + j) * nx_pad + i;
-            float2 w[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
-                           make_float2(0.f, 0.f)};
+        const int off1 = has1 ? nx_pad : 0;                // column j0 + 1 (re-read j0 at the last odd column)
+        for (int c = ty; c < nc; c += G) {
+            const float2 *src = part + ((size_t)c * ny + j0) * nx_pad + i;
+            float2 w0[4], w1[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) w0[e] = w1[e] = make_float2(0.f, 0.f);
             int p = 0;
             for (; p + 3 < ksplit; p += 4) {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) w[e] = cadd(w[e], src[(size_t)(p + e) * pstride]);
+                for (int e = 0; e < 4; ++e) {
+                    const float2 *q = src + (size_t)(p + e) * pstride;
+                    w0[e] = cadd(w0[e], q[0]);
+                    w1[e] = cadd(w1[e], q[off1]);
+                }
             }
-            for (; p < ksplit; ++p) w[0] = cadd(w[0], src[(size_t)p * pstride]);
-            const float2 wsum = cadd(cadd(w[0], w[1]), cadd(w[2], w[3]));
-            acc = cadd(acc, cmulc(maps[c * npix + (size_t)i * ny + j], wsum));
+            for (; p < ksplit; ++p) {
+                const float2 *q = src + (size_t)p * pstride;
+                w0[0] = cadd(w0[0], q[0]);
+                w1[0] = cadd(w1[0], q[off1]);
+            }
+            const float2 *s = maps + c * npix + (size_t)i * ny + j0;
+            acc0 = cadd(acc0, cmulc(s[0], cadd(cadd(w0[0], w0[1]), cadd(w0[2], w0[3]))));
+            if (has1) acc1 = cadd(acc1, cmulc(s[1], cadd(cadd(w1[0], w1[1]), cadd(w1[2], w1[3]))));
         }
     }
-    grp[ty][tx] = acc;
+    grp[ty][0][tx] = acc0;
+    grp[ty][1][tx] = acc1;
     __syncthreads();
     double dot = 0.0;
-    if (ty == 0 && i < nx) {
-        float2 v = grp[0][tx];
-#pragma unroll
-        for (int g = 1; g < kReduceGroups; ++g) v = cadd(v, grp[g][tx]);
+    // rows 0 and 1 finish columns j0 and j0 + 1
+    if (ty < 2 && i < nx && (ty == 0 || has1)) {
+        const int j = j0 + ty;
+        float2 v = grp[0][ty][tx];
+        for (int g = 1; g < G; ++g) v = cadd(v, grp[g][ty][tx]);
         if (tv_src) {
             const float2 t = theta_h_theta_at(tv_src, i, j, nx, ny);
             v.x = fmaf(half_beta, t.x, v.x);
@@ -302,8 +318,8 @@ int ew_blocks(int n) { return max(1, min(kEwMaxBlocks, ceil_div(n, kEwThreads)))
 
 cudaError_t launch_adj_reduce(mri_plan *p, const float2 *maps, float2 *out, const ReduceEpilogue &e,
                               cudaStream_t s) {
-    dim3 grid(ceil_div(p->nx, 32), p->ny);
-    adj_reduce_kernel<<<grid, dim3(32, kReduceGroups), 0, s>>>(p->part, p->ksplit, p->nc, p->nx, p->ny, p->nx_pad, maps, out,
+    dim3 grid(ceil_div(p->nx, 32), ceil_div(p->ny, 2));
+    adj_reduce_kernel<<<grid, dim3(32, std::min(p->nc, kReduceGroups)), 0, s>>>(p->part, p->ksplit, p->nc, p->nx, p->ny, p->nx_pad, maps, out,
                                                    e.tv_src, e.half_beta, e.dot_src, p->scal, p->partials, e.skip);
     return cudaGetLastError();
 }

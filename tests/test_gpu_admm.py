@@ -151,3 +151,26 @@ def test_admm_zero_iterations_returns_zero_image(mr):
     d = oracle.measurements(p)
     x, _, _ = _run(mr, p, d, "fp32", with_hist=False, iters=(0, 5))
     assert np.all(x == 0)
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp32"])
+def test_resume_continues_bit_for_bit(mr, precision):
+    # (x, eta) is the whole ADMM state: 3 steps, save, 4 more from the saved
+    # state = 7 steps in one call, bit for bit (direct launches and graphs)
+    p = synth.config_small()
+    g, d = _golden(p)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        with mr.Plan(p.nx, p.ny, p.nc, _dev(p.traj, torch.float32), precision) as plan:
+            k, m = _dev(d), _dev(p.maps)
+            whole, eta_whole = mr.admm_resume(plan, k, m, p.lam, p.beta, 7, p.cg_iters)
+            plain = mr.admm_reconstruct(plan, k, m, p.lam, p.beta, 7, p.cg_iters)
+            x3, eta3 = mr.admm_resume(plan, k, m, p.lam, p.beta, 3, p.cg_iters)
+            x7, eta7 = mr.admm_resume(plan, k, m, p.lam, p.beta, 4, p.cg_iters, x0=x3.clone(), eta0=eta3.clone())
+            plan.set_graphs(False)
+            x7d, _ = mr.admm_resume(plan, k, m, p.lam, p.beta, 4, p.cg_iters, x0=x3.clone(), eta0=eta3.clone())
+            plan.sync_status()
+    assert torch.equal(whole, plain)
+    assert torch.equal(x7, whole) and torch.equal(eta7, eta_whole)
+    assert torch.equal(x7d, whole)
+    assert not torch.equal(x3, whole)
