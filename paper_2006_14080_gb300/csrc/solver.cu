@@ -94,11 +94,12 @@ __global__ void __launch_bounds__(32 * kReduceGroups, 2)
     grp[ty][1][tx] = acc1;
     __syncthreads();
     double dot = 0.0;
-    // rows 0 and 1 finish columns j0 and j0 + 1
-    if (ty < 2 && i < nx && (ty == 0 || has1)) {
-        const int j = j0 + ty;
-        float2 v = grp[0][ty][tx];
-        for (int g = 1; g < G; ++g) v = cadd(v, grp[g][ty][tx]);
+    // rows 0 and 1 finish columns j0 and j0 + 1 (row 0 both when G = 1)
+    for (int col = ty; col < 2; col += G) {
+        if (i >= nx || (col == 1 && !has1)) continue;
+        const int j = j0 + col;
+        float2 v = grp[0][col][tx];
+        for (int g = 1; g < G; ++g) v = cadd(v, grp[g][col][tx]);
         if (tv_src) {
             const float2 t = theta_h_theta_at(tv_src, i, j, nx, ny);
             v.x = fmaf(half_beta, t.x, v.x);
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(32 * kReduceGroups, 2)
         out[(size_t)i * ny + j] = v;
         if (dot_src) {
             const float2 dv = dot_src[(size_t)i * ny + j];
-            dot = (double)dv.x * (double)v.x + (double)dv.y * (double)v.y;
+            dot += (double)dv.x * (double)v.x + (double)dv.y * (double)v.y;
         }
     }
     if (dot_src) {
