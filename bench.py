@@ -32,8 +32,13 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-# single-reconstruction workloads: N=128 (the headline) and N=256
-WORKLOADS = {"n128": synth.config_medium, "n256": synth.config_large}
+# single-reconstruction workloads: N=128 (the headline), N=256, and the
+# paper's two shapes with its Table I parameters and tolerance exits
+WORKLOADS = {"n128": synth.config_medium, "n256": synth.config_large,
+             "paper128x64": synth.config_paper_128x64, "paper1024x512": synth.config_paper_1024x512}
+# the paper's own times for its shapes (TPU v3, float32-equivalent; context, another machine)
+PAPER_TIMES_S = {"paper_128x64_c12_s13x128": {"2 TPU v3 cores": 0.1363, "16 TPU v3 cores": 0.0356},
+                 "paper_1024x512_c12_s101x1024": {"128 TPU v3 cores": 3.387, "2048 TPU v3 cores": 0.286}}
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
@@ -139,8 +144,11 @@ def workload_name(p) -> str:
 
 
 def metric_name(p) -> str:
-    return (f"ADMM recon/s, N={p.nx} image, {p.nc} coils, {p.spokes} golden-angle spokes x {p.readout} samples, "
-            f"{p.admm_iters} ADMM x {p.cg_iters} CG, BF16x3 tensor-core NUDFT (TF32 and FP32 forms beside)")
+    size = f"N={p.nx}" if p.nx == p.ny else f"{p.nx}x{p.ny}"
+    angles = "golden-angle" if p.angles == "golden" else "uniform-angle"
+    tol = "" if not (p.rtol or p.atol) else f" (rtol {p.rtol:g}, atol {p.atol:g} exits)"
+    return (f"ADMM recon/s, {size} image, {p.nc} coils, {p.spokes} {angles} spokes x {p.readout} samples, "
+            f"{p.admm_iters} ADMM x {p.cg_iters} CG{tol}, BF16x3 tensor-core NUDFT (TF32 and FP32 forms beside)")
 
 
 def normal_ops_per_recon(p):
@@ -253,11 +261,13 @@ def run_gpu(args, rank, world, local_rank):
                 d_k.copy_(h_k, non_blocking=True)
                 d_maps.copy_(h_maps, non_blocking=True)
                 plan.set_trajectory(d_traj)
-                mr.admm_reconstruct(plan, d_k, d_maps, p.lam, p.beta, p.admm_iters, p.cg_iters, out=out)
+                mr.admm_reconstruct(plan, d_k, d_maps, p.lam, p.beta, p.admm_iters, p.cg_iters, out=out,
+                                    rtol=p.rtol, atol=p.atol)
                 h_out.copy_(out, non_blocking=True)
             else:
                 plan.set_trajectory(traj)
-                mr.admm_reconstruct(plan, kspace, maps, p.lam, p.beta, p.admm_iters, p.cg_iters, out=out)
+                mr.admm_reconstruct(plan, kspace, maps, p.lam, p.beta, p.admm_iters, p.cg_iters, out=out,
+                                    rtol=p.rtol, atol=p.atol)
 
         for _ in range(warmup):
             one()
@@ -356,7 +366,18 @@ def run_gpu(args, rank, world, local_rank):
     executed = 3.0 * flops_prod  # hi*hi + hi*lo + lo*hi bf16 tensor products
     achieved = executed / (dom_avg_ms * 1e-3) / 1e12
     peak_tf = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
-    useful_tflops_step = normal_ops_per_recon(p) * 2 * flops_prod / (total_ms / args.steps * 1e-3) / 1e12
+    # with tolerance exits the operator count is data-dependent: count the
+    # ADMM steps one reconstruction takes and leave the TFLOP/s out
+    tol_steps = None
+    if p.rtol > 0 or p.atol > 0:
+        import torch
+        with mr.Plan(p.nx, p.ny, p.nc, traj, "bf16x3") as plan_c:
+            ah = torch.full((p.admm_iters,), -1.0, dtype=torch.float64, device=dev)
+            mr.admm_reconstruct(plan_c, kspace, maps, p.lam, p.beta, p.admm_iters, p.cg_iters, out=out,
+                                rtol=p.rtol, atol=p.atol, alpha_hist=ah)
+            tol_steps = int((ah >= 0).sum().item())
+    useful_tflops_step = None if tol_steps is not None else \
+        normal_ops_per_recon(p) * 2 * flops_prod / (total_ms / args.steps * 1e-3) / 1e12
     dom_kernel = "adj_tc_kernel" if dom == "adj" else "fwd_tc_kernel"
     traffic, traffic_src = captured_traffic(dom_kernel, p.name)
     nrmse_vs_golden = None
@@ -378,7 +399,8 @@ def run_gpu(args, rank, world, local_rank):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "bf16x3/f32",
-        "data": "synthetic (seeded ellipse phantom, Gaussian coil maps, golden-angle radial, 0.5% noise)",
+        "data": f"synthetic (seeded ellipse phantom, Gaussian coil maps, {p.angles}-angle radial, "
+                f"{100 * p.noise_level:g}% noise)",
         "config": {"workload": workload_name(p), "nx": p.nx, "ny": p.ny, "coils": p.nc, "spokes": p.spokes,
                    "readout": p.readout, "admm_iters": p.admm_iters, "cg_iters": p.cg_iters, "lambda": p.lam,
                    "beta": p.beta, "l2": "flushed (512 MB write) between timed steps",
@@ -409,6 +431,9 @@ def run_gpu(args, rank, world, local_rank):
         "gemm_peaks_tflops": gemm_peaks,
         "tf32_form": None,
         "nrmse_vs_fp64_oracle": nrmse_vs_golden,
+        "tolerances": None if tol_steps is None else {"rtol": p.rtol, "atol": p.atol, "admm_steps_taken": tol_steps,
+                                                      "admm_iters_max": p.admm_iters, "cg_iters_max": p.cg_iters},
+        "paper_context_s": PAPER_TIMES_S.get(p.name),
         "clocks": clocks,
     }
     if tf32 is not None:
@@ -698,10 +723,12 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--workload", default="n128", choices=["n128", "n256", "batch64", "serve"],
+    ap.add_argument("--workload", default="n128",
+                    choices=["n128", "n256", "paper128x64", "paper1024x512", "batch64", "serve"],
                     help="n128: the single N=128 reconstruction (default); n256: the N=256, 32-coil "
-                         "reconstruction; batch64: 64 heterogeneous reconstructions in one batched launch; "
-                         "serve: the serving loop under Poisson arrivals")
+                         "reconstruction; paper128x64 / paper1024x512: the paper's two shapes with its Table I "
+                         "parameters and tolerance exits; batch64: 64 heterogeneous reconstructions in one "
+                         "batched launch; serve: the serving loop under Poisson arrivals")
     ap.add_argument("--batch-items", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-inflight", type=int, default=8)
@@ -724,7 +751,7 @@ def main():
                          "n256 (whose FP32 form takes about half a minute per reconstruction)")
     args = ap.parse_args()
     if not args.forms:
-        args.forms = "bf16x3,e2e,tf32" if args.workload == "n256" else "bf16x3,e2e,fp32,tf32"
+        args.forms = "bf16x3,e2e,tf32" if args.workload in ("n256", "paper1024x512") else "bf16x3,e2e,fp32,tf32"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -223,7 +223,9 @@ int plan_create(mri_plan **out, int nx, int ny, int nk, int nc, const float *tra
         }
     }
     p->nx_pad = round_up(nx, 64);
-    p->ny_pad = round_up(ny, 16);
+    // UMMA N granularity; an image wider than one UMMA (256) is processed in
+    // column parts of 256
+    p->ny_pad = ny <= 256 ? round_up(ny, 16) : round_up(ny, 256);
     p->kx = round_up(2 * nx, 64);
     p->kk = round_up(2 * nk, 64);
     p->nk_pad = round_up(nk, 32);
@@ -375,7 +377,7 @@ MRI_API size_t mri_plan_estimate_bytes(int nx, int ny, int nk, int nc, int preci
         return 0;
     }
     t.nx_pad = round_up(nx, 64);
-    t.ny_pad = round_up(ny, 16);
+    t.ny_pad = ny <= 256 ? round_up(ny, 16) : round_up(ny, 256);
     t.kx = round_up(2 * nx, 64);
     t.kk = round_up(2 * nk, 64);
     t.nk_pad = round_up(nk, 32);

@@ -82,7 +82,7 @@ struct mri_plan {
     // BF16 hi/lo real-embedded operands (tensor-core path)
     int kx = 0;       // round_up(2*nx, 64): K of the forward product
     int kk = 0;       // round_up(2*nk, 64): K of the adjoint product
-    int ny_pad = 0;   // round_up(ny, 16): UMMA N granularity
+    int ny_pad = 0;   // round_up(ny, 16), or round_up(ny, 256) past 256: UMMA N granularity
     int nx_pad = 0;   // round_up(nx, 64): image rows per adjoint M tile group
     int fwd_coils_per_tile = 0, fwd_block_n = 0, fwd_n_tiles = 0, fwd_m_tiles = 0;
     int adj_m_tiles = 0, adj_block_n = 0;

@@ -17,7 +17,8 @@
 // Forward  (Eq. 1):  Z = A_x (S_c . X) for all coils at once
 //     A  = embedded A_x          [2 nk][kx]        static, TMA
 //     B  = (S_c . X)^T per coil  [nc * ny_pad][kx] written by fwd_operand_kernel, TMA
-//   tile: 128 rows (64 samples) x block_n columns (whole coils).  The
+//   tile: 128 rows (64 samples) x block_n columns (whole coils, or 256-column
+//   sub-tiles of one coil wider than that).  The
 //   epilogue forms y_c[k] = sum_j Z[k][j] A_y[k][j] from TMEM, with the
 //   matching 64-sample x 32-column tiles of A_y staged in shared memory by a
 //   TMA warp.
@@ -26,7 +27,8 @@
 //                                that a TMA warp stages, written to tensor
 //                                memory (the UMMAs read A from TMEM)
 //     B  = conj(A_y)^T           [ny_pad][kk]      static, TMA
-//   tile: 128 rows (64 pixels of one coil) x ny_pad columns, split over
+//   tile: 128 rows (64 pixels of one coil) x ny_pad columns (at most 256; a
+//   wider image is covered in column parts of 256), split over
 //   contiguous k-space ranges; the epilogue writes partial images that
 //   launch_adj_reduce sums in a fixed order (the paper's cross-core sum).
 //
@@ -80,6 +82,11 @@ constexpr int kMaxKbPerSplit = MRI_ADJ_MAX_KB_PER_SPLIT;  // adjoint: K blocks (
 struct FwdParams {
     float2 *y;  // [nc][y_ld]
     int y_ld, nk, ny_pad, nc, cpt, block_n, n_tiles, num_kb, stages, ay_stages;
+    // columns of one coil wider than one UMMA (ny_pad > 256): each tile is
+    // n_parts sub-tiles of pw = 256 columns, one accumulator each, whose row
+    // sums the epilogue adds before it writes y; otherwise n_parts = 1 and
+    // pw = ny_pad (the whole coil, cpt coils per tile)
+    int n_parts, pw;
     int cm, num_groups;  // cluster size; groups = ceil(m_tiles / cm) * n_tiles
     uint32_t tmem_cols;
     const DevScalars *sc;
@@ -89,7 +96,9 @@ struct FwdParams {
 
 struct AdjParams {
     float2 *part;  // [ksplit][nc][ny][nx_pad]
-    int nx, ny, ny_pad, nx_pad, nc, tiles_per_coil, m_tiles, kb_per_split, num_kb;
+    // ny_pad here is the tile width (the UMMA N, at most 256); an image wider
+    // than that is covered by n_parts column parts of it, each its own unit
+    int nx, ny, ny_pad, nx_pad, nc, tiles_per_coil, m_tiles, kb_per_split, num_kb, n_parts;
     int stages, raw_stages;
     int n_acc, a_col0;   // accumulator buffers in TMEM; first TMEM column of the A slots
     int cm, num_groups;  // cluster size; groups = m_tiles * ksplit / cm
@@ -206,7 +215,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     uint32_t *tmem_slot = (uint32_t *)(bars + 2 * S + 2 * R + 5);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_jc = (P.ny_pad + 31) / 32;
+    const int n_jc = (P.pw + 31) / 32;  // A_y chunks of 32 columns per sub-tile
     const int rank = (int)cluster_ctarank();
     const int cluster_id = blockIdx.x / P.cm, num_clusters = gridDim.x / P.cm;
     const uint32_t b_slice = b_bytes / (uint32_t)P.cm;  // rows block_n / cm
@@ -253,8 +262,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             int issued_mask = 0;
             for (int g = cluster_id; g < P.num_groups && !*abort_flag; g += num_clusters) {
                 const int m_blk = (g / P.n_tiles) * P.cm + rank, n_blk = g % P.n_tiles;
-                const int b_row = n_blk * P.block_n + rank * (P.block_n / P.cm);
+                for (int part = 0; part < P.n_parts; ++part)
                 for (int kb = 0; kb < P.num_kb; ++kb) {
+                    const int b_row = n_blk * P.cpt * P.ny_pad + part * P.pw + rank * (P.block_n / P.cm);
                     if (!mbar_wait(empty0 + 8 * rg.stage, rg.phase ^ 1, abort_flag, kWaitLimitNs)) break;
                     const uint32_t sbase = smem_u32(smem + (size_t)rg.stage * stage_bytes);
                     const uint32_t fb = full0 + 8 * rg.stage;
@@ -287,7 +297,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             Ring rg;
             int lt = 0;
             bool issued_any = false;
-            for (int g = cluster_id; g < P.num_groups; g += num_clusters, ++lt) {
+            // one accumulator per (group, sub-tile), in the loader's order
+            for (int t = 0;; ++t, ++lt) {
+                if (cluster_id + (t / P.n_parts) * num_clusters >= P.num_groups) break;
                 const int a = lt & 1;
                 const uint32_t ap = (lt >> 1) & 1;
                 if (!mbar_wait(tempty0 + 8 * a, ap ^ 1, abort_flag, kWaitLimitNs)) break;
@@ -350,12 +362,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             int issued_mask = 0;
             for (int g = cluster_id; g < P.num_groups && !*abort_flag; g += num_clusters) {
                 const int m_blk = (g / P.n_tiles) * P.cm + rank;
+                for (int part = 0; part < P.n_parts; ++part)
                 for (int jc = 0; jc < n_jc; ++jc) {
                     if (!mbar_wait(yempty0 + 8 * rg.stage, rg.phase ^ 1, abort_flag, kWaitLimitNs)) break;
                     const uint32_t yb = yfull0 + 8 * rg.stage;
                     mbar_arrive_expect_tx(yb, kAyChunkBytes);
                     tma_load_2d(smem_u32(ay_ring + (size_t)rg.stage * kAyChunkBytes), &t_ay, yb,
-                                m_blk * (kTcBlockM), jc * 32);
+                                m_blk * (kTcBlockM), part * P.pw + jc * 32);
                     issued_phase[rg.stage] = rg.phase;
                     issued_mask |= 1 << rg.stage;
                     rg.next(R);
@@ -373,15 +386,19 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
         Ring yr;
         int lt = 0;
-        for (int g = cluster_id; g < P.num_groups; g += num_clusters, ++lt) {
+        float s0[kMaxCoilsPerTile], s1[kMaxCoilsPerTile];  // row sums, carried across a tile's sub-tiles
+        for (int t = 0;; ++t, ++lt) {
+            const int g = cluster_id + (t / P.n_parts) * num_clusters, part = t % P.n_parts;
+            if (g >= P.num_groups) break;
             const int a = lt & 1;
             const uint32_t ap = (lt >> 1) & 1;
             if (!mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) break;
             fence_after_sync();
             const int m_blk = (g / P.n_tiles) * P.cm + rank, n_blk = g % P.n_tiles;
-            float s0[kMaxCoilsPerTile], s1[kMaxCoilsPerTile];
+            if (part == 0) {
 #pragma unroll
-            for (int cs = 0; cs < kMaxCoilsPerTile; ++cs) s0[cs] = s1[cs] = 0.f;
+                for (int cs = 0; cs < kMaxCoilsPerTile; ++cs) s0[cs] = s1[cs] = 0.f;
+            }
             bool ok = true;
             for (int jc = 0; jc < n_jc; ++jc) {
                 if (!mbar_wait(yfull0 + 8 * yr.stage, yr.phase, abort_flag, kWaitLimitNs)) {
@@ -400,11 +417,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                     c0[q] = o ? -w.y : w.x;
                     c1[q] = o ? w.x : w.y;
                 }
-                const bool full32 = P.ny_pad - 32 * jc >= 32;
+                const bool full32 = P.pw - 32 * jc >= 32;
 #pragma unroll
                 for (int cs = 0; cs < kMaxCoilsPerTile; ++cs) {
                     if (cs < P.cpt) {
-                        const uint32_t col = (uint32_t)(a * P.block_n + cs * P.ny_pad + 32 * jc);
+                        const uint32_t col = (uint32_t)(a * P.block_n + cs * P.pw + 32 * jc);
                         float v[32];
                         if (full32) {
                             tmem_ld_32cols(tmem_base + lane_base + col, v);
@@ -427,6 +444,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             fence_before_sync();
             mbar_arrive(tempty0 + 8 * a);
             if (!ok) break;
+            if (part != P.n_parts - 1) continue;  // the coil's row sums are complete after its last sub-tile
             const int kappa = m_blk * (kTcBlockM / 2) + kk_local;
 #pragma unroll
             for (int cs = 0; cs < kMaxCoilsPerTile; ++cs) {
@@ -448,6 +466,18 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     }
     if (threadIdx.x == 0 && *abort_flag) atomicExch(P.status, kStatusTimeout);
     cluster_sync();  // no CTA leaves while a peer may still multicast into it or arrive on its barriers
+}
+
+// Work unit u of the adjoint: k-space split p, column part, and tile m (the
+// coil fastest, m = ib * nc + c); the cm units of a cluster group share p and
+// the part, hence the conj(A_y) rows.
+struct AdjUnit {
+    int p, part, m;
+};
+__device__ __forceinline__ AdjUnit adj_unit(const AdjParams &P, int u) {
+    const int per_split = P.m_tiles * P.n_parts;
+    const int rem = u % per_split;
+    return AdjUnit{u / per_split, rem / P.m_tiles, rem % P.m_tiles};
 }
 
 // ---------------------------------------------------------------------------
@@ -535,9 +565,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         uint32_t issued_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int issued_mask = 0;
         for (int g = cluster_id; g < P.num_groups && !*abort_flag; g += num_clusters) {
-            const int u = g * P.cm + rank;
-            const int p = u / P.m_tiles;
-            const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
+            const AdjUnit un = adj_unit(P, g * P.cm + rank);
+            const int kb0 = un.p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
             bool ok = true;
             for (int kb = kb0; kb < kb1; ++kb) {
                 if (!mbar_wait(rfull0 + 8 * rr.stage, rr.phase, abort_flag, kWaitLimitNs) ||
@@ -549,7 +578,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                 if (threadIdx.x == 0) {
                     // this CTA's 1/cm of the conj(A_y) rows, delivered to the whole cluster
                     const uint32_t sb = smem_u32(smem + (size_t)rs.stage * stage_bytes) + rank * b_slice;
-                    const int b_row = rank * (P.ny_pad / P.cm);
+                    const int b_row = un.part * P.ny_pad + rank * (P.ny_pad / P.cm);
                     mbar_arrive_expect_tx(fb, 2u * b_bytes);
                     const int x0 = kb * kTcBlockK, x1 = x0 + (kTf32 ? kTcBlockK / 2 : 0);
                     if (P.cm > 1) {
@@ -648,9 +677,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
             int lt = 0;
             bool issued_any = false;
             for (int g = cluster_id; g < P.num_groups; g += num_clusters, ++lt) {
-                const int u = g * P.cm + rank;
-                const int p = u / P.m_tiles;
-                const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
+                const AdjUnit un = adj_unit(P, g * P.cm + rank);
+                const int kb0 = un.p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
                 const int a = lt % NA;
                 const uint32_t ap = (lt / NA) & 1;
                 if (!mbar_wait(tempty0 + 8 * a, ap ^ 1, abort_flag, kWaitLimitNs)) break;
@@ -709,10 +737,9 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
             uint32_t issued_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             int issued_mask = 0;
             for (int g = cluster_id; g < P.num_groups && !*abort_flag; g += num_clusters) {
-                const int u = g * P.cm + rank;
-                const int p = u / P.m_tiles, m = u % P.m_tiles;
-                const int c = m % P.nc, ib = m / P.nc;
-                const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
+                const AdjUnit un = adj_unit(P, g * P.cm + rank);
+                const int c = un.m % P.nc, ib = un.m / P.nc;
+                const int kb0 = un.p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
                 for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(rempty0 + 8 * rg.stage, rg.phase ^ 1, abort_flag, kWaitLimitNs)) break;
                     const uint32_t rb = rfull0 + 8 * rg.stage;
@@ -738,15 +765,15 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
         int lt = 0;
         for (int g = cluster_id; g < P.num_groups; g += num_clusters, ++lt) {
-            const int u = g * P.cm + rank;
+            const AdjUnit un = adj_unit(P, g * P.cm + rank);
             const int a = lt % NA;
             const uint32_t ap = (lt / NA) & 1;
             if (!mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) break;
             fence_after_sync();
-            const int p = u / P.m_tiles, m = u % P.m_tiles;
-            const int c = m % P.nc, ib = m / P.nc;
+            const int c = un.m % P.nc, ib = un.m / P.nc;
             const int i = ib * 64 + ii;
-            float *dst = reinterpret_cast<float *>(P.part + ((size_t)p * P.nc + c) * P.ny * P.nx_pad) + 2 * i + o;
+            const int j0 = un.part * P.ny_pad;  // first image column of this part
+            float *dst = reinterpret_cast<float *>(P.part + ((size_t)un.p * P.nc + c) * P.ny * P.nx_pad) + 2 * i + o;
             const size_t jstride = 2 * (size_t)P.nx_pad;
             const uint32_t col0 = (uint32_t)(a * P.ny_pad);
             int jc = 0;
@@ -755,14 +782,14 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                 tmem_ld_32cols(tmem_base + lane_base + col0 + jc, v);
 #pragma unroll
                 for (int q = 0; q < 32; ++q)
-                    if (jc + q < P.ny) dst[(size_t)(jc + q) * jstride] = v[q];
+                    if (j0 + jc + q < P.ny) dst[(size_t)(j0 + jc + q) * jstride] = v[q];
             }
             if (jc < P.ny_pad) {
                 float v[16];
                 tmem_ld_16cols(tmem_base + lane_base + col0 + jc, v);
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
-                    if (jc + q < P.ny) dst[(size_t)(jc + q) * jstride] = v[q];
+                    if (j0 + jc + q < P.ny) dst[(size_t)(j0 + jc + q) * jstride] = v[q];
             }
             fence_before_sync();
             mbar_arrive(tempty0 + 8 * a);
@@ -853,12 +880,13 @@ void adj_smem_plan(const mri_plan *p, int *stages, int *raw_stages, size_t *byte
                    int *a_col0 = nullptr) {
     // shared memory holds the B (conj A_y) stages and the raw A_x^H / y ring;
     // TMEM holds the accumulators and one 64-column A slot per stage
-    const int stage = 2 * p->ny_pad * 128;
+    const int bn = p->adj_block_n;  // UMMA N: conj(A_y) rows per tile
+    const int stage = 2 * bn * 128;
     const int raw = kRawBytes + kRawYBytes;
     int s = 4, r = 0, na = 2, col0 = 0;
     for (; s >= 2; --s) {
-        na = (round_up(2 * p->ny_pad, 64) + 64 * s <= 512) ? 2 : 1;
-        col0 = round_up(na * p->ny_pad, 64);
+        na = (round_up(2 * bn, 64) + 64 * s <= 512) ? 2 : 1;
+        col0 = round_up(na * bn, 64);
         if (col0 + 64 * s > 512) continue;
         r = std::min(6, (kMaxSmem - kSmemSlack - s * stage) / raw);
         if (r >= (s > 2 ? 3 : 2)) break;
@@ -880,8 +908,8 @@ bool tc_supported(const mri_plan *p, std::string *why) {
         *why = "needs an sm_103 GPU (found sm_" + std::to_string(major) + std::to_string(minor) + ")";
         return false;
     }
-    if (round_up(p->ny, 16) > 256) {
-        *why = "ny up to 256 is supported by the tensor-core kernels";
+    if (p->ny > 1024) {
+        *why = "ny up to 1024 is supported by the tensor-core kernels";
         return false;
     }
     if (!get_encode_fn()) {
@@ -892,11 +920,12 @@ bool tc_supported(const mri_plan *p, std::string *why) {
 }
 
 int tc_plan_tiling(mri_plan *p) {
-    // forward: whole coils per N tile
+    // forward: whole coils per N tile, or one coil in sub-tiles of 256
+    // columns when it is wider than one UMMA (ny_pad is then a multiple of 256)
     const int cpt_max = std::min(kMaxCoilsPerTile, std::max(1, 256 / p->ny_pad));
     const int n_tiles = ceil_div(p->nc, cpt_max);
     p->fwd_coils_per_tile = ceil_div(p->nc, n_tiles);
-    p->fwd_block_n = p->fwd_coils_per_tile * p->ny_pad;
+    p->fwd_block_n = p->ny_pad > 256 ? 256 : p->fwd_coils_per_tile * p->ny_pad;
     p->fwd_n_tiles = ceil_div(p->nc, p->fwd_coils_per_tile);
     p->fwd_m_tiles = ceil_div(2 * p->nk, kTcBlockM);
     // adjoint: 64 pixels (128 embedded rows) of one coil per M tile; split K
@@ -910,7 +939,8 @@ int tc_plan_tiling(mri_plan *p) {
     // products); 32 blocks keep the operator within 1e-5 for any nk at a
     // cost of 6% on that adjoint (more partial images to write and sum)
     p->adj_m_tiles = p->nc * (p->nx_pad / 64);
-    p->adj_block_n = p->ny_pad;
+    p->adj_block_n = std::min(p->ny_pad, 256);
+    const int n_parts = p->ny_pad / p->adj_block_n;  // column parts of the image, one unit each
     const int num_kb = p->kk / kTcBlockK;
     long best_cost = -1;
     int best_split = 1;
@@ -918,7 +948,7 @@ int tc_plan_tiling(mri_plan *p) {
     for (int split = min_split; split <= std::min(num_kb, 128); ++split) {
         const int per = ceil_div(num_kb, split);
         const int eff = ceil_div(num_kb, per);
-        const long waves = ceil_div(p->adj_m_tiles * eff, p->num_sms);
+        const long waves = ceil_div(p->adj_m_tiles * n_parts * eff, p->num_sms);
         const long cost = waves * per + (long)eff / 8;  // makespan in K blocks, small penalty per split
         if (best_cost < 0 || cost < best_cost) {
             best_cost = cost;
@@ -1016,7 +1046,7 @@ bool tc_cluster_valid_fwd(const mri_plan *p, int cm) {
 
 bool tc_cluster_valid_adj(const mri_plan *p, int cm) {
     if (cm != 1 && cm != 2 && cm != 4 && cm != 8) return false;
-    return cm == 1 || (p->adj_m_tiles % cm == 0 && p->ny_pad % (8 * cm) == 0 && cm <= p->num_sms);
+    return cm == 1 || (p->adj_m_tiles % cm == 0 && p->adj_block_n % (8 * cm) == 0 && cm <= p->num_sms);
 }
 
 int tc_set_clusters(mri_plan *p, int fwd_cm, int adj_cm) {
@@ -1030,7 +1060,7 @@ int tc_set_clusters(mri_plan *p, int fwd_cm, int adj_cm) {
     bool ok = make_operand_maps(p, &p->tm_bfwd_hi, &p->tm_bfwd_lo, p->bfwd_hi, p->bfwd_lo, p->bfwd_t, p->kx,
                                 (uint64_t)p->nc * p->ny_pad, p->fwd_block_n / fwd_cm) &&
               make_operand_maps(p, &p->tm_badj_hi, &p->tm_badj_lo, p->badj_hi, p->badj_lo, p->badj_t, p->kk,
-                                p->ny_pad, p->ny_pad / adj_cm);
+                                p->ny_pad, p->adj_block_n / adj_cm);
     if (!ok) {
         set_error("cuTensorMapEncodeTiled failed");
         return MRI_ERR_CUDA;
@@ -1070,6 +1100,8 @@ cudaError_t launch_fwd_tc(mri_plan *p, const float2 *image, const float2 *maps, 
     P.cpt = p->fwd_coils_per_tile;
     P.block_n = p->fwd_block_n;
     P.n_tiles = p->fwd_n_tiles;
+    P.n_parts = p->ny_pad > 256 ? p->ny_pad / 256 : 1;
+    P.pw = p->ny_pad > 256 ? 256 : p->ny_pad;
     P.num_kb = p->kx / kTcBlockK;
     P.cm = p->fwd_cluster;
     P.num_groups = ceil_div(p->fwd_m_tiles, P.cm) * p->fwd_n_tiles;
@@ -1095,7 +1127,8 @@ cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
     P.part = p->part;
     P.nx = p->nx;
     P.ny = p->ny;
-    P.ny_pad = p->ny_pad;
+    P.ny_pad = p->adj_block_n;  // the tile width
+    P.n_parts = p->ny_pad / p->adj_block_n;
     P.nx_pad = p->nx_pad;
     P.nc = p->nc;
     P.tiles_per_coil = p->nx_pad / 64;
@@ -1103,7 +1136,7 @@ cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
     P.kb_per_split = p->ksplit_blocks;
     P.num_kb = p->kk / kTcBlockK;
     P.cm = p->adj_cluster;
-    P.num_groups = p->adj_m_tiles * p->ksplit / P.cm;
+    P.num_groups = p->adj_m_tiles * P.n_parts * p->ksplit / P.cm;
     size_t smem;
     adj_smem_plan(p, &P.stages, &P.raw_stages, &smem, &P.n_acc, &P.a_col0);
     P.tmem_cols = tmem_cols_for(P.a_col0 + 64 * P.stages);

@@ -156,6 +156,9 @@ class Problem:
     admm_iters: int
     cg_iters: int
     seed: int
+    rtol: float = 0.0         # Alg. 4 relative-change exit (0: fixed count)
+    atol: float = 0.0         # Alg. 2 residual exit (0: fixed count)
+    angles: str = "golden"    # spoke angles: "golden" or "uniform"
 
     @property
     def nk(self) -> int:
@@ -174,7 +177,7 @@ def make_problem(name: str, n: int, nc: int, spokes: int, readout: int, *, seed:
     noise = unit_noise(rng, nc, spokes * readout)
     traj = radial_trajectory(spokes, readout, golden=golden)
     return Problem(name, nx, ny, nc, spokes, readout, traj, img, maps, noise, noise_level,
-                   lam, beta, admm_iters, cg_iters, seed)
+                   lam, beta, admm_iters, cg_iters, seed, angles="golden" if golden else "uniform")
 
 
 # The three single-reconstruction workloads (seeds fixed so that every consumer
@@ -195,6 +198,32 @@ def config_large() -> Problem:
     """N=256, 32 coils, 128 golden-angle spokes x 512 samples, 50 ADMM x 10 CG."""
     return make_problem("n256_c32_s128x512", 256, 32, 128, 512, seed=1003, golden=True,
                         noise_level=0.005, lam=1e-3, beta=1.0, admm_iters=50, cg_iters=10)
+
+
+# The paper's own workload shapes (Section V-VI, Table I parameters, with its
+# tolerance exits): a 128 x 64 grid from 13 radial readouts of 128 samples
+# per coil, and a 1024 x 512 grid from 101 readouts of 1024 samples per coil
+# (103,424 per coil), 12 coils each.  Uniform spoke angles: the eightfold
+# undersampling keeps every eighth readout of a uniform set.
+TABLE1 = dict(lam=1e-7, beta=1.0, admm_iters=5, cg_iters=20, rtol=1e-4, atol=1e-6)
+
+
+def config_paper_128x64() -> Problem:
+    """128 x 64 image, 12 coils, 13 x 128 samples per coil, Table I parameters."""
+    p = make_problem("paper_128x64_c12_s13x128", 128, 12, 13, 128, seed=1004, golden=False, noise_level=0.005,
+                     lam=TABLE1["lam"], beta=TABLE1["beta"], admm_iters=TABLE1["admm_iters"],
+                     cg_iters=TABLE1["cg_iters"], ny=64)
+    p.rtol, p.atol = TABLE1["rtol"], TABLE1["atol"]
+    return p
+
+
+def config_paper_1024x512() -> Problem:
+    """1024 x 512 image, 12 coils, 101 x 1024 samples per coil, Table I parameters."""
+    p = make_problem("paper_1024x512_c12_s101x1024", 1024, 12, 101, 1024, seed=1005, golden=False,
+                     noise_level=0.005, lam=TABLE1["lam"], beta=TABLE1["beta"], admm_iters=TABLE1["admm_iters"],
+                     cg_iters=TABLE1["cg_iters"], ny=512)
+    p.rtol, p.atol = TABLE1["rtol"], TABLE1["atol"]
+    return p
 
 
 def batch_item(j: int) -> Problem:

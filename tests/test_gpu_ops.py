@@ -56,6 +56,8 @@ SHAPES = [
     (64, 48, 2, 16, 128),     # non-square, ny a multiple of 16 only
     (100, 72, 5, 9, 61),      # odd sample count
     (32, 32, 4, 16, 64),      # the small workload's shape
+    (48, 300, 2, 5, 64),      # wider than one UMMA: two 256-column parts, the second mostly padding
+    (40, 520, 1, 3, 50),      # three parts, one coil, ragged samples
 ]
 
 

@@ -67,7 +67,7 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("shape", [(40, 40, 3, 7, 100), (64, 48, 2, 16, 128), (100, 72, 5, 9, 61)])
+@pytest.mark.parametrize("shape", [(40, 40, 3, 7, 100), (64, 48, 2, 16, 128), (100, 72, 5, 9, 61), (36, 300, 2, 4, 64)])
 def test_tf32_products_match_emulation(shape):
     import paper_2006_14080_gb300 as mr
     nx, ny, nc, spokes, readout = shape

@@ -314,3 +314,13 @@ def test_admm_table1_parameters_stop_on_tolerances():
     # every step but the last saw alpha above rtol^2 (Alg. 4 loop condition)
     assert np.all(a[:-1] > t1["admm_rtol"] ** 2)
     assert out["steps"] == t1["admm_max_iterations"] or a[-1] <= t1["admm_rtol"] ** 2
+
+
+def test_table1_constants_of_the_paper_workloads():
+    # the input generator's Table I constants are the stored Table I values
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table1_admm_params.json")) as fh:
+        t1 = json.load(fh)
+    assert synth.TABLE1 == dict(lam=t1["lambda"], beta=t1["beta"], admm_iters=t1["admm_max_iterations"],
+                                cg_iters=t1["cg_max_iterations"], rtol=t1["admm_rtol"], atol=t1["cg_atol"])
