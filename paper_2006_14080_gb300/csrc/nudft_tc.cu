@@ -28,7 +28,7 @@
 //                                memory (the UMMAs read A from TMEM)
 //     B  = conj(A_y)^T           [ny_pad][kk]      static, TMA
 //   tile: 128 rows (64 pixels of one coil) x ny_pad columns (at most 256; a
-//   wider image is covered in column parts of 256), split over
+//   wider image takes one launch per 256-column part), split over
 //   contiguous k-space ranges; the epilogue writes partial images that
 //   launch_adj_reduce sums in a fixed order (the paper's cross-core sum).
 //
@@ -96,9 +96,11 @@ struct FwdParams {
 
 struct AdjParams {
     float2 *part;  // [ksplit][nc][ny][nx_pad]
-    // ny_pad here is the tile width (the UMMA N, at most 256); an image wider
-    // than that is covered by n_parts column parts of it, each its own unit
-    int nx, ny, ny_pad, nx_pad, nc, tiles_per_coil, m_tiles, kb_per_split, num_kb, n_parts;
+    // ny_pad here is the tile width (the UMMA N, at most 256).  An image wider
+    // than that is covered by one launch per 256-column part: part points at
+    // the part's first column, b_row0 is its first conj(A_y) row and ny_lim
+    // the number of its columns that lie inside the image.
+    int nx, ny, ny_pad, nx_pad, nc, tiles_per_coil, m_tiles, kb_per_split, num_kb, ny_lim, b_row0;
     int stages, raw_stages;
     int n_acc, a_col0;   // accumulator buffers in TMEM; first TMEM column of the A slots
     int cm, num_groups;  // cluster size; groups = m_tiles * ksplit / cm
@@ -468,18 +470,6 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     cluster_sync();  // no CTA leaves while a peer may still multicast into it or arrive on its barriers
 }
 
-// Work unit u of the adjoint: k-space split p, column part, and tile m (the
-// coil fastest, m = ib * nc + c); the cm units of a cluster group share p and
-// the part, hence the conj(A_y) rows.
-struct AdjUnit {
-    int p, part, m;
-};
-__device__ __forceinline__ AdjUnit adj_unit(const AdjParams &P, int u) {
-    const int per_split = P.m_tiles * P.n_parts;
-    const int rem = u % per_split;
-    return AdjUnit{u / per_split, rem / P.m_tiles, rem % P.m_tiles};
-}
-
 // ---------------------------------------------------------------------------
 // Adjoint product.  The dynamic operand U (real-embedded, hi/lo) is written by
 // the producer warps straight into tensor memory with tcgen05.st; the UMMAs
@@ -565,8 +555,9 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         uint32_t issued_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int issued_mask = 0;
         for (int g = cluster_id; g < P.num_groups && !*abort_flag; g += num_clusters) {
-            const AdjUnit un = adj_unit(P, g * P.cm + rank);
-            const int kb0 = un.p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
+            const int u = g * P.cm + rank;
+            const int p = u / P.m_tiles;
+            const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
             bool ok = true;
             for (int kb = kb0; kb < kb1; ++kb) {
                 if (!mbar_wait(rfull0 + 8 * rr.stage, rr.phase, abort_flag, kWaitLimitNs) ||
@@ -578,7 +569,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                 if (threadIdx.x == 0) {
                     // this CTA's 1/cm of the conj(A_y) rows, delivered to the whole cluster
                     const uint32_t sb = smem_u32(smem + (size_t)rs.stage * stage_bytes) + rank * b_slice;
-                    const int b_row = un.part * P.ny_pad + rank * (P.ny_pad / P.cm);
+                    const int b_row = P.b_row0 + rank * (P.ny_pad / P.cm);
                     mbar_arrive_expect_tx(fb, 2u * b_bytes);
                     const int x0 = kb * kTcBlockK, x1 = x0 + (kTf32 ? kTcBlockK / 2 : 0);
                     if (P.cm > 1) {
@@ -677,8 +668,9 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
             int lt = 0;
             bool issued_any = false;
             for (int g = cluster_id; g < P.num_groups; g += num_clusters, ++lt) {
-                const AdjUnit un = adj_unit(P, g * P.cm + rank);
-                const int kb0 = un.p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
+                const int u = g * P.cm + rank;
+                const int p = u / P.m_tiles;
+                const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
                 const int a = lt % NA;
                 const uint32_t ap = (lt / NA) & 1;
                 if (!mbar_wait(tempty0 + 8 * a, ap ^ 1, abort_flag, kWaitLimitNs)) break;
@@ -737,9 +729,10 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
             uint32_t issued_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             int issued_mask = 0;
             for (int g = cluster_id; g < P.num_groups && !*abort_flag; g += num_clusters) {
-                const AdjUnit un = adj_unit(P, g * P.cm + rank);
-                const int c = un.m % P.nc, ib = un.m / P.nc;
-                const int kb0 = un.p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
+                const int u = g * P.cm + rank;
+                const int p = u / P.m_tiles, m = u % P.m_tiles;
+                const int c = m % P.nc, ib = m / P.nc;
+                const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
                 for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(rempty0 + 8 * rg.stage, rg.phase ^ 1, abort_flag, kWaitLimitNs)) break;
                     const uint32_t rb = rfull0 + 8 * rg.stage;
@@ -765,15 +758,15 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
         int lt = 0;
         for (int g = cluster_id; g < P.num_groups; g += num_clusters, ++lt) {
-            const AdjUnit un = adj_unit(P, g * P.cm + rank);
+            const int u = g * P.cm + rank;
             const int a = lt % NA;
             const uint32_t ap = (lt / NA) & 1;
             if (!mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) break;
             fence_after_sync();
-            const int c = un.m % P.nc, ib = un.m / P.nc;
+            const int p = u / P.m_tiles, m = u % P.m_tiles;
+            const int c = m % P.nc, ib = m / P.nc;
             const int i = ib * 64 + ii;
-            const int j0 = un.part * P.ny_pad;  // first image column of this part
-            float *dst = reinterpret_cast<float *>(P.part + ((size_t)un.p * P.nc + c) * P.ny * P.nx_pad) + 2 * i + o;
+            float *dst = reinterpret_cast<float *>(P.part + ((size_t)p * P.nc + c) * P.ny * P.nx_pad) + 2 * i + o;
             const size_t jstride = 2 * (size_t)P.nx_pad;
             const uint32_t col0 = (uint32_t)(a * P.ny_pad);
             int jc = 0;
@@ -782,14 +775,14 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                 tmem_ld_32cols(tmem_base + lane_base + col0 + jc, v);
 #pragma unroll
                 for (int q = 0; q < 32; ++q)
-                    if (j0 + jc + q < P.ny) dst[(size_t)(j0 + jc + q) * jstride] = v[q];
+                    if (jc + q < P.ny_lim) dst[(size_t)(jc + q) * jstride] = v[q];
             }
             if (jc < P.ny_pad) {
                 float v[16];
                 tmem_ld_16cols(tmem_base + lane_base + col0 + jc, v);
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
-                    if (j0 + jc + q < P.ny) dst[(size_t)(j0 + jc + q) * jstride] = v[q];
+                    if (jc + q < P.ny_lim) dst[(size_t)(jc + q) * jstride] = v[q];
             }
             fence_before_sync();
             mbar_arrive(tempty0 + 8 * a);
@@ -940,7 +933,7 @@ int tc_plan_tiling(mri_plan *p) {
     // cost of 6% on that adjoint (more partial images to write and sum)
     p->adj_m_tiles = p->nc * (p->nx_pad / 64);
     p->adj_block_n = std::min(p->ny_pad, 256);
-    const int n_parts = p->ny_pad / p->adj_block_n;  // column parts of the image, one unit each
+    const int n_parts = p->ny_pad / p->adj_block_n;  // column parts of the image, one launch each
     const int num_kb = p->kk / kTcBlockK;
     long best_cost = -1;
     int best_split = 1;
@@ -948,7 +941,7 @@ int tc_plan_tiling(mri_plan *p) {
     for (int split = min_split; split <= std::min(num_kb, 128); ++split) {
         const int per = ceil_div(num_kb, split);
         const int eff = ceil_div(num_kb, per);
-        const long waves = ceil_div(p->adj_m_tiles * n_parts * eff, p->num_sms);
+        const long waves = n_parts * ceil_div(p->adj_m_tiles * eff, p->num_sms);  // one launch per part
         const long cost = waves * per + (long)eff / 8;  // makespan in K blocks, small penalty per split
         if (best_cost < 0 || cost < best_cost) {
             best_cost = cost;
@@ -1128,7 +1121,6 @@ cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
     P.nx = p->nx;
     P.ny = p->ny;
     P.ny_pad = p->adj_block_n;  // the tile width
-    P.n_parts = p->ny_pad / p->adj_block_n;
     P.nx_pad = p->nx_pad;
     P.nc = p->nc;
     P.tiles_per_coil = p->nx_pad / 64;
@@ -1136,7 +1128,7 @@ cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
     P.kb_per_split = p->ksplit_blocks;
     P.num_kb = p->kk / kTcBlockK;
     P.cm = p->adj_cluster;
-    P.num_groups = p->adj_m_tiles * P.n_parts * p->ksplit / P.cm;
+    P.num_groups = p->adj_m_tiles * p->ksplit / P.cm;
     size_t smem;
     adj_smem_plan(p, &P.stages, &P.raw_stages, &smem, &P.n_acc, &P.a_col0);
     P.tmem_cols = tmem_cols_for(P.a_col0 + 64 * P.stages);
@@ -1144,14 +1136,23 @@ cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
     P.skip = skip;
     P.status = &p->scal->status;
     const int grid = P.cm * std::min(P.num_groups, p->adj_grid / P.cm);
+    // one launch per 256-column part of the image (one launch when ny <= 256)
+    const int n_parts = p->ny_pad / p->adj_block_n;
     timing_begin(p, s);
-    cudaError_t e = p->precision == MRI_TF32
-                        ? launch_clustered(adj_tc_kernel<true>, grid, kAdjThreads, smem, P.cm, s, p->tm_badj_hi,
-                                           p->tm_badj_lo, p->tm_axT, p->tm_y, P)
-                        : launch_clustered(adj_tc_kernel<false>, grid, kAdjThreads, smem, P.cm, s, p->tm_badj_hi,
-                                           p->tm_badj_lo, p->tm_axT, p->tm_y, P);
+    cudaError_t e = cudaSuccess;
+    for (int part = 0; part < n_parts && e == cudaSuccess; ++part) {
+        const int j0 = part * p->adj_block_n;
+        P.part = p->part + (size_t)j0 * p->nx_pad;  // column j0 of every (split, coil) plane
+        P.ny_lim = p->ny - j0;
+        P.b_row0 = j0;
+        e = p->precision == MRI_TF32
+                ? launch_clustered(adj_tc_kernel<true>, grid, kAdjThreads, smem, P.cm, s, p->tm_badj_hi,
+                                   p->tm_badj_lo, p->tm_axT, p->tm_y, P)
+                : launch_clustered(adj_tc_kernel<false>, grid, kAdjThreads, smem, P.cm, s, p->tm_badj_hi,
+                                   p->tm_badj_lo, p->tm_axT, p->tm_y, P);
+        p->launches += 1;
+    }
     timing_end(p, s);
-    p->launches += 1;
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
