@@ -515,14 +515,36 @@ def run_batch(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        batch.reconstruct(items)
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES") else local_rank
+    with ClockSampler(gpu_index) as clk:
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            batch.reconstruct(items)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        # end to end: every step copies each item's k-space and coil maps in from
+        # pinned host memory and its image out, around the same batched launch
+        host = [(it["kspace"].cpu().pin_memory(), it["coil_maps"].cpu().pin_memory(),
+                 torch.empty_like(it["out"], device="cpu").pin_memory()) for it in items]
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            ev2[i][0].record(stream)
+            for it, (hk, hm, _) in zip(items, host):
+                it["kspace"].copy_(hk, non_blocking=True)
+                it["coil_maps"].copy_(hm, non_blocking=True)
+            batch.reconstruct(items)
+            for it, (_, _, ho) in zip(items, host):
+                ho.copy_(it["out"], non_blocking=True)
+            ev2[i][1].record(stream)
+        torch.cuda.synchronize()
     total_ms = max_over_ranks_fn(dist, dev)(sum(a.elapsed_time(b) for a, b in ev))
+    e2e_ms = max_over_ranks_fn(dist, dev)(sum(a.elapsed_time(b) for a, b in ev2))
+    h2d = sum(hk.numel() * hk.element_size() + hm.numel() * hm.element_size() for hk, hm, _ in host)
+    d2h = sum(ho.numel() * ho.element_size() for _, _, ho in host)
     launches = batch.launch_count()
     batch.close()
     for pl in plans:
@@ -540,7 +562,10 @@ def run_batch(args, rank, world, local_rank):
         "config": {"workload": f"batch{n}_hetero_admm30x8", "items": n, "l2": "flushed between timed steps",
                    "resident_plan_bytes": resident},
         "useful_tflops": useful * args.steps / (total_ms / 1e3) / 1e12,
-        "gpu_launches": launches,
+        "e2e": {"value": whole_job_rate(n * args.steps, e2e_ms, world), "unit": "recon/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches * args.steps,  # kernels in one replay x timed steps
+        "clocks": clk.summary(),
     }
 
 
