@@ -217,8 +217,10 @@ void worker_loop(mri_server *s) {
                     s->latencies_ms.push_back(
                         std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count());
                 } else {
-                    // clear the plan's status word before it serves again
+                    // clear the plan's status word before it serves again, on
+                    // any stream (a failure path: waiting here is acceptable)
                     cudaMemsetAsync(&j->entry->plan->scal->status, 0, sizeof(int), s->streams[j->slot]);
+                    cudaStreamSynchronize(s->streams[j->slot]);
                     fail_job(s, j, MRI_ERR_TIMEOUT,
                              "a bounded device-side wait gave up (status " + std::to_string(dev_status) + ")");
                 }
