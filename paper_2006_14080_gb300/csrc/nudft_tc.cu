@@ -64,6 +64,7 @@ constexpr int kFwdThreads = 224;                  // w0 TMA, w1 UMMA, w2 A_y TMA
 // adjoint: producer warps (8 or 16), then the UMMA warp, 4 epilogue warps, the TMA warp
 constexpr int kAdjProducerWarps = MRI_ADJ_PRODUCER_WARPS;
 static_assert(kAdjProducerWarps == 8 || kAdjProducerWarps == 16, "8 or 16 producer warps");
+constexpr int kAdjProducers = 32 * kAdjProducerWarps;
 constexpr int kAdjMmaWarp = kAdjProducerWarps;
 constexpr int kAdjLoaderWarp = kAdjProducerWarps + 5;
 constexpr int kAdjThreads = 32 * (kAdjProducerWarps + 6);
@@ -229,11 +230,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         }
         for (int r = 0; r < R; ++r) {
             mbar_init(yfull0 + 8 * r, 1);
-            mbar_init(yempty0 + 8 * r, 4);  // one arrival per epilogue warp
+            mbar_init(yempty0 + 8 * r, 128);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull0 + 8 * a, 1);
-            mbar_init(tempty0 + 8 * a, 4);  // one arrival per epilogue warp
+            mbar_init(tempty0 + 8 * a, 128);
         }
         mbar_init(fin, 1);
         *abort_flag = 0;
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             if (g >= P.num_groups) break;
             const int a = lt & 1;
             const uint32_t ap = (lt >> 1) & 1;
-            if (!mbar_wait_warp(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) break;
+            if (!mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) break;
             fence_after_sync();
             const int m_blk = (g / P.n_tiles) * P.cm + rank, n_blk = g % P.n_tiles;
             if (part == 0) {
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             }
             bool ok = true;
             for (int jc = 0; jc < n_jc; ++jc) {
-                if (!mbar_wait_warp(yfull0 + 8 * yr.stage, yr.phase, abort_flag, kWaitLimitNs)) {
+                if (!mbar_wait(yfull0 + 8 * yr.stage, yr.phase, abort_flag, kWaitLimitNs)) {
                     ok = false;
                     break;
                 }
@@ -439,11 +440,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                         }
                     }
                 }
-                mbar_arrive_warp(yempty0 + 8 * yr.stage);
+                mbar_arrive(yempty0 + 8 * yr.stage);
                 yr.next(R);
             }
             fence_before_sync();
-            mbar_arrive_warp(tempty0 + 8 * a);
+            mbar_arrive(tempty0 + 8 * a);
             if (!ok) break;
             if (part != P.n_parts - 1) continue;  // the coil's row sums are complete after its last sub-tile
             const int kappa = m_blk * (kTcBlockM / 2) + kk_local;
@@ -507,16 +508,16 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(full0 + 8 * s, kAdjProducerWarps + 1);  // producer warps + the B loads' expect_tx arrival
+            mbar_init(full0 + 8 * s, kAdjProducers + 1);  // producer threads + the B loads' expect_tx arrival
             mbar_init(empty0 + 8 * s, P.cm);  // released by the UMMA commits of every CTA of the cluster
         }
         for (int r = 0; r < R; ++r) {
             mbar_init(rfull0 + 8 * r, 1);
-            mbar_init(rempty0 + 8 * r, kAdjProducerWarps);
+            mbar_init(rempty0 + 8 * r, kAdjProducers);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull0 + 8 * a, 1);
-            mbar_init(tempty0 + 8 * a, 4);  // one arrival per epilogue warp
+            mbar_init(tempty0 + 8 * a, 128);
         }
         mbar_init(fin, 1);
         *abort_flag = 0;
@@ -559,9 +560,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
             const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
             bool ok = true;
             for (int kb = kb0; kb < kb1; ++kb) {
-                const bool got = mbar_wait(rfull0 + 8 * rr.stage, rr.phase, abort_flag, kWaitLimitNs) &&
-                                 mbar_wait(empty0 + 8 * rs.stage, rs.phase ^ 1, abort_flag, kWaitLimitNs);
-                if (!__all_sync(0xffffffffu, got)) {
+                if (!mbar_wait(rfull0 + 8 * rr.stage, rr.phase, abort_flag, kWaitLimitNs) ||
+                    !mbar_wait(empty0 + 8 * rs.stage, rs.phase ^ 1, abort_flag, kWaitLimitNs)) {
                     ok = false;
                     break;
                 }
@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                         iw[4 * c + 2] = i1;
                         iw[4 * c + 3] = r1;
                     }
-                    mbar_arrive_warp(rempty0 + 8 * rr.stage);
+                    mbar_arrive(rempty0 + 8 * rr.stage);
                     rr.next(R);
                     // the Re-row thread (o = 0) keeps its Re pairs and receives the
                     // partner's; the Im-row thread likewise, in sample order
@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                         split_embed(cmulc(make_float2(av.z, av.w), make_float2(yv.z, yv.w)), hre[2 * c + 1],
                                     lre[2 * c + 1], him[2 * c + 1], lim[2 * c + 1]);
                     }
-                    mbar_arrive_warp(rempty0 + 8 * rr.stage);
+                    mbar_arrive(rempty0 + 8 * rr.stage);
                     rr.next(R);
                     // the Re-row thread keeps its Re words and receives the
                     // partner's; the Im-row thread likewise, in sample order
@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                 }
                 tmem_wait_st();
                 fence_before_sync();
-                mbar_arrive_warp(fb);
+                mbar_arrive(fb);
                 rs.next(S);
             }
             if (!ok) break;
@@ -761,7 +761,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
             const int u = g * P.cm + rank;
             const int a = lt % NA;
             const uint32_t ap = (lt / NA) & 1;
-            if (!mbar_wait_warp(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) break;
+            if (!mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) break;
             fence_after_sync();
             const int p = u / P.m_tiles, m = u % P.m_tiles;
             const int c = m % P.nc, ib = m / P.nc;
@@ -785,7 +785,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                     if (jc + q < P.ny_lim) dst[(size_t)(jc + q) * jstride] = v[q];
             }
             fence_before_sync();
-            mbar_arrive_warp(tempty0 + 8 * a);
+            mbar_arrive(tempty0 + 8 * a);
         }
     }
 

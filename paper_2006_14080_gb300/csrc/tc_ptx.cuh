@@ -65,21 +65,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
-// One arrival for the whole warp once every lane has got here (the barrier
-// counts warps): each lane's prior memory and tcgen05 accesses are ordered
-// before it by the warp synchronisation, the arrival itself releases them.
-__device__ __forceinline__ void mbar_arrive_warp(uint32_t bar) {
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
-}
-
-// mbar_wait taken by every lane of the warp, with a warp-uniform result (a
-// lane that gave up makes the whole warp give up, so that no lane is left
-// behind at a later warp synchronisation).
-__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort, uint64_t limit_ns) {
-    return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort, limit_ns));
-}
-
 // ---------------------------------------------------------------- TMA
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *m) {
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)m) : "memory");
