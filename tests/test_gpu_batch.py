@@ -39,7 +39,7 @@ def _problems():
     return [small] + others
 
 
-@pytest.mark.parametrize("precision", ["bf16x3", "fp32"])
+@pytest.mark.parametrize("precision", ["bf16x3", "fp32", "tf32"])
 def test_batch_equals_alone(mr, precision):
     probs = _problems()
     side = torch.cuda.Stream()
@@ -72,7 +72,7 @@ def test_batch_equals_alone(mr, precision):
     # the N=32 member against the FP64 oracle (bar as in test_gpu_admm)
     g = oracle.admm(probs[0].traj, probs[0].maps, oracle.measurements(probs[0]), probs[0].lam, probs[0].beta,
                     probs[0].admm_iters, probs[0].cg_iters)["x"]
-    assert np.linalg.norm(first[0] - g) / np.linalg.norm(g) <= 1e-2
+    assert np.linalg.norm(first[0] - g) / np.linalg.norm(g) <= (5e-2 if precision == "tf32" else 1e-2)  # TF32: the paper's 5% (Section V)
 
 
 def test_batch_rejects_shared_plans(mr):

@@ -59,7 +59,7 @@ def test_estimate_matches_plan(mr, precision):
     assert mr.estimate_plan_bytes(0, 8, 8, 1, precision) == 0
 
 
-@pytest.mark.parametrize("precision", ["bf16x3", "fp32"])
+@pytest.mark.parametrize("precision", ["bf16x3", "fp32", "tf32"])
 def test_serve_mix_equals_alone(mr, precision):
     probs = _problems()
     data = [oracle.measurements(p) for p in probs]
@@ -86,7 +86,7 @@ def test_serve_mix_equals_alone(mr, precision):
         assert np.array_equal(_direct(mr, probs[q], data[q], precision), alone[q])
     g = oracle.admm(probs[0].traj, probs[0].maps, data[0], probs[0].lam, probs[0].beta, probs[0].admm_iters,
                     probs[0].cg_iters)["x"]
-    assert np.linalg.norm(alone[0] - g) / np.linalg.norm(g) <= 1e-2
+    assert np.linalg.norm(alone[0] - g) / np.linalg.norm(g) <= (5e-2 if precision == "tf32" else 1e-2)  # TF32: the paper's 5% (Section V)
 
 
 def test_serve_budget_admission(mr):
