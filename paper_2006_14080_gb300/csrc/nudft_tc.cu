@@ -937,7 +937,10 @@ int tc_plan_tiling(mri_plan *p) {
     const int num_kb = p->kk / kTcBlockK;
     long best_cost = -1;
     int best_split = 1;
-    const int min_split = std::min(128, ceil_div(num_kb, kMaxKbPerSplit));
+    // the TF32 form's operand rounding (~4e-4) dwarfs the accumulation error of
+    // long runs (2.5e-5 at 108 blocks), so it takes fewer, longer splits
+    const int max_kb_per_split = p->precision == MRI_TF32 ? 4 * kMaxKbPerSplit : kMaxKbPerSplit;
+    const int min_split = std::min(128, ceil_div(num_kb, max_kb_per_split));
     for (int split = min_split; split <= std::min(num_kb, 128); ++split) {
         const int per = ceil_div(num_kb, split);
         const int eff = ceil_div(num_kb, per);

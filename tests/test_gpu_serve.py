@@ -50,9 +50,10 @@ def _direct(mr, p, d, precision):
             return x.cpu().numpy()
 
 
-@pytest.mark.parametrize("precision", ["bf16x3", "fp32"])
+@pytest.mark.parametrize("precision", ["bf16x3", "fp32", "tf32"])
 def test_estimate_matches_plan(mr, precision):
-    for (nx, ny, nc, nk) in [(32, 32, 4, 1024), (40, 56, 2, 720), (128, 128, 12, 16384), (64, 48, 3, 999)]:
+    for (nx, ny, nc, nk) in [(32, 32, 4, 1024), (40, 56, 2, 720), (128, 128, 12, 16384), (64, 48, 3, 999),
+                             (48, 300, 2, 4096)]:
         traj = torch.zeros((nk, 2), dtype=torch.float32, device="cuda")
         with mr.Plan(nx, ny, nc, traj, precision) as plan:
             assert mr.estimate_plan_bytes(nx, ny, nk, nc, precision) == plan.device_bytes()
