@@ -107,7 +107,6 @@ struct mri_plan {
     float2 *part = nullptr;   // [ksplit][nc][ny][nx_pad] adjoint partial images
     int ksplit = 1;           // k-space splits of the adjoint product
     int ksplit_blocks = 0;    // K blocks per split (tensor path) or samples per split (FP32)
-    int adj_chunk_blocks = 0; // tensor path: K blocks per accumulation run (a split holds whole runs)
 
     // solver state
     float2 *x = nullptr, *xprev = nullptr, *r = nullptr, *d = nullptr, *ad = nullptr;

@@ -75,10 +75,6 @@ constexpr int kMaxCoilsPerTile = 4;
 #define MRI_ADJ_MAX_KB_PER_SPLIT 32
 #endif
 constexpr int kMaxKbPerSplit = MRI_ADJ_MAX_KB_PER_SPLIT;  // adjoint: K blocks (32 samples each) per k-space split
-#ifndef MRI_ADJ_MAX_RUNS_PER_SLOT
-#define MRI_ADJ_MAX_RUNS_PER_SLOT 8
-#endif
-constexpr int kMaxRunsPerSlot = MRI_ADJ_MAX_RUNS_PER_SLOT;  // adjoint: accumulation runs summed into one slot
 
 // Work split of both kernels: clusters of `cm` CTAs process groups of cm
 // tiles (units) in lockstep; the operand shared by the group (B) is loaded
@@ -105,10 +101,6 @@ struct AdjParams {
     // the part's first column, b_row0 is its first conj(A_y) row and ny_lim
     // the number of its columns that lie inside the image.
     int nx, ny, ny_pad, nx_pad, nc, tiles_per_coil, m_tiles, kb_per_split, num_kb, ny_lim, b_row0;
-    // a unit's K range (kb_per_split blocks, one partial-image slot) is summed
-    // in runs of kb_per_chunk blocks, each in a fresh TMEM accumulator, and the
-    // epilogue adds the runs into the slot in order
-    int kb_per_chunk;
     int stages, raw_stages;
     int n_acc, a_col0;   // accumulator buffers in TMEM; first TMEM column of the A slots
     int cm, num_groups;  // cluster size; groups = m_tiles * ksplit / cm
@@ -675,22 +667,17 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
             Ring rg;
             int lt = 0;
             bool issued_any = false;
-            bool ok = true;
-            for (int g = cluster_id; g < P.num_groups && ok; g += num_clusters) {
+            for (int g = cluster_id; g < P.num_groups; g += num_clusters, ++lt) {
                 const int u = g * P.cm + rank;
                 const int p = u / P.m_tiles;
                 const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
-              for (int kc = kb0; kc < kb1; kc += P.kb_per_chunk, ++lt) {
-                const int kc1 = min(kb1, kc + P.kb_per_chunk);
                 const int a = lt % NA;
                 const uint32_t ap = (lt / NA) & 1;
-                if (!mbar_wait(tempty0 + 8 * a, ap ^ 1, abort_flag, kWaitLimitNs)) {
-                    ok = false;
-                    break;
-                }
+                if (!mbar_wait(tempty0 + 8 * a, ap ^ 1, abort_flag, kWaitLimitNs)) break;
                 fence_after_sync();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(a * P.ny_pad);
-                for (int kb = kc; kb < kc1; ++kb) {
+                bool ok = true;
+                for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(full0 + 8 * rg.stage, rg.phase, abort_flag, kWaitLimitNs)) {
                         ok = false;
                         break;
@@ -705,14 +692,14 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
 #pragma unroll
                         for (int kk = 0; kk < 8; ++kk) {
                             const uint64_t db = sdesc_kmajor_sw128((kk < 4 ? sb_hi : sb_lo) + (kk & 3) * 32);
-                            umma_tf32_tmem_a(d_tmem, ta_hi + 8 * kk, db, idesc, (kb != kc || kk != 0) ? 1u : 0u);
+                            umma_tf32_tmem_a(d_tmem, ta_hi + 8 * kk, db, idesc, (kb != kb0 || kk != 0) ? 1u : 0u);
                         }
                     } else {
 #pragma unroll
                         for (int kk = 0; kk < kTcBlockK / 16; ++kk) {
                             const uint64_t dbh = sdesc_kmajor_sw128(sb_hi + kk * 32),
                                            dbl = sdesc_kmajor_sw128(sb_lo + kk * 32);
-                            umma_f16_tmem_a(d_tmem, ta_hi + 8 * kk, dbh, idesc, (kb != kc || kk != 0) ? 1u : 0u);
+                            umma_f16_tmem_a(d_tmem, ta_hi + 8 * kk, dbh, idesc, (kb != kb0 || kk != 0) ? 1u : 0u);
                             umma_f16_tmem_a(d_tmem, ta_hi + 8 * kk, dbl, idesc, 1u);
                             umma_f16_tmem_a(d_tmem, ta_lo + 8 * kk, dbh, idesc, 1u);
                         }
@@ -727,7 +714,6 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                 }
                 if (!ok) break;
                 umma_commit(tfull0 + 8 * a);
-              }
             }
             // all UMMAs and their commits (some arrive in other CTAs) have
             // landed before the block leaves the cluster barrier below
@@ -771,50 +757,35 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         const int ii = row >> 1, o = row & 1;
         const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
         int lt = 0;
-        bool ok = true;
-        for (int g = cluster_id; g < P.num_groups && ok; g += num_clusters) {
+        for (int g = cluster_id; g < P.num_groups; g += num_clusters, ++lt) {
             const int u = g * P.cm + rank;
+            const int a = lt % NA;
+            const uint32_t ap = (lt / NA) & 1;
+            if (!mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) break;
+            fence_after_sync();
             const int p = u / P.m_tiles, m = u % P.m_tiles;
             const int c = m % P.nc, ib = m / P.nc;
             const int i = ib * 64 + ii;
             float *dst = reinterpret_cast<float *>(P.part + ((size_t)p * P.nc + c) * P.ny * P.nx_pad) + 2 * i + o;
             const size_t jstride = 2 * (size_t)P.nx_pad;
-            const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
-            // the unit's runs in order: the first writes the slot, the others add to it
-            for (int kc = kb0; kc < kb1; kc += P.kb_per_chunk, ++lt) {
-                const bool first = kc == kb0;
-                const int a = lt % NA;
-                const uint32_t ap = (lt / NA) & 1;
-                if (!mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) {
-                    ok = false;
-                    break;
-                }
-                fence_after_sync();
-                const uint32_t col0 = (uint32_t)(a * P.ny_pad);
-                int jc = 0;
-                for (; jc + 32 <= P.ny_pad; jc += 32) {
-                    float v[32];
-                    tmem_ld_32cols(tmem_base + lane_base + col0 + jc, v);
+            const uint32_t col0 = (uint32_t)(a * P.ny_pad);
+            int jc = 0;
+            for (; jc + 32 <= P.ny_pad; jc += 32) {
+                float v[32];
+                tmem_ld_32cols(tmem_base + lane_base + col0 + jc, v);
 #pragma unroll
-                    for (int q = 0; q < 32; ++q)
-                        if (jc + q < P.ny_lim) {
-                            float *d = dst + (size_t)(jc + q) * jstride;
-                            *d = first ? v[q] : *d + v[q];
-                        }
-                }
-                if (jc < P.ny_pad) {
-                    float v[16];
-                    tmem_ld_16cols(tmem_base + lane_base + col0 + jc, v);
-#pragma unroll
-                    for (int q = 0; q < 16; ++q)
-                        if (jc + q < P.ny_lim) {
-                            float *d = dst + (size_t)(jc + q) * jstride;
-                            *d = first ? v[q] : *d + v[q];
-                        }
-                }
-                fence_before_sync();
-                mbar_arrive(tempty0 + 8 * a);
+                for (int q = 0; q < 32; ++q)
+                    if (jc + q < P.ny_lim) dst[(size_t)(jc + q) * jstride] = v[q];
             }
+            if (jc < P.ny_pad) {
+                float v[16];
+                tmem_ld_16cols(tmem_base + lane_base + col0 + jc, v);
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (jc + q < P.ny_lim) dst[(size_t)(jc + q) * jstride] = v[q];
+            }
+            fence_before_sync();
+            mbar_arrive(tempty0 + 8 * a);
         }
     }
 
@@ -980,23 +951,7 @@ int tc_plan_tiling(mri_plan *p) {
             best_split = eff;
         }
     }
-    // runs of at most max_kb_per_split blocks (the accumulation limit) ...
-    const int per = ceil_div(num_kb, best_split);
-    const int runs = ceil_div(num_kb, per);
-    // ... grouped g at a time into one partial-image slot per unit, when that
-    // leaves enough units to balance the SMs: fewer slots to write, hold and
-    // sum (at N=256 and 65536 samples: 8 slots of 1 GB / 8 instead of 64)
-    int best_g = 1;
-    const double ideal = (double)p->adj_m_tiles * runs / p->num_sms;
-    const double eff1 = ideal / ceil_div(p->adj_m_tiles * runs, p->num_sms);
-    for (int g = 2; g <= kMaxRunsPerSlot; ++g) {
-        const long units = (long)p->adj_m_tiles * ceil_div(runs, g);
-        if (units < 4L * p->num_sms) break;
-        const double eff = ideal / ((double)ceil_div((int)units, p->num_sms) * g);
-        if (eff >= 0.95 * eff1) best_g = g;
-    }
-    p->adj_chunk_blocks = per;
-    p->ksplit_blocks = best_g * per;
+    p->ksplit_blocks = ceil_div(num_kb, best_split);
     p->ksplit = ceil_div(num_kb, p->ksplit_blocks);
     int s, r;
     size_t fb, ab;
@@ -1174,7 +1129,6 @@ cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
     P.tiles_per_coil = p->nx_pad / 64;
     P.m_tiles = p->adj_m_tiles;
     P.kb_per_split = p->ksplit_blocks;
-    P.kb_per_chunk = p->adj_chunk_blocks;
     P.num_kb = p->kk / kTcBlockK;
     P.cm = p->adj_cluster;
     P.num_groups = p->adj_m_tiles * p->ksplit / P.cm;

@@ -216,20 +216,3 @@ def test_tuning_table_sets_new_plans(mr, tmp_path):
         cfg = plan.config()
         assert (cfg["fwd_cluster"], cfg["adj_cluster"]) == (tuned["fwd_cluster"], tuned["adj_cluster"])
     mr.tuning_clear()
-
-
-def test_grouped_accumulation_runs_match_oracle(mr):
-    # 16 coils and 38912 samples: 38 accumulation runs of at most 32 K blocks
-    # per tile, enough units to group two runs per partial-image slot (the
-    # epilogue adds the second run into the slot); the adjoint must still meet
-    # the operator bar
-    nx = ny = 128
-    nc, spokes, readout = 16, 152, 256
-    maps, traj, x, y = _case(nx, ny, nc, spokes, readout, seed=77)
-    with mr.Plan(nx, ny, nc, _dev(traj, torch.float32), "bf16x3") as plan:
-        cfg = plan.config()
-        adj = mr.nudft_adjoint(plan, _dev(y), _dev(maps)).cpu().numpy()
-        plan.sync_status()
-    runs = -(-2 * traj.shape[0] // 64 // 32)
-    assert cfg["adj_ksplit"] < runs, cfg  # grouped
-    assert _rel(adj, oracle.adjoint(traj, y, maps)) <= OP_TOL["bf16x3"]
