@@ -64,10 +64,11 @@ int dev_alloc(mri_plan *p, T **ptr, size_t count) {
 void free_plan(mri_plan *p, cudaStream_t free_stream = nullptr) {
     if (!p) return;
     invalidate_graph(p);
-    void *bufs[] = {p->ax,      p->ay,      p->axT,     p->ayT,    p->afwd_hi, p->afwd_lo, p->badj_hi,
-                    p->badj_lo, p->bfwd_hi, p->bfwd_lo, p->afwd_t, p->badj_t,  p->bfwd_t,  p->bsx,
-                    p->y,       p->part,    p->x,       p->xprev,  p->r,       p->d,       p->ad,
-                    p->b,       p->fhd,     p->mu,      p->eta,    p->partials, p->scal};
+    void *bufs[] = {p->ax,      p->ay,      p->axT,     p->axP,    p->axQ,      p->ayT,  p->afwd_hi,
+                    p->afwd_lo, p->badj_hi, p->badj_lo, p->bfwd_hi, p->bfwd_lo, p->afwd_t, p->badj_t,
+                    p->bfwd_t,  p->bsx,     p->y,       p->part,   p->x,        p->xprev, p->r,
+                    p->d,       p->ad,      p->b,       p->fhd,    p->mu,       p->eta,   p->partials,
+                    p->scal};
     for (void *q : bufs)
         if (q) {
             if (p->pool)
@@ -244,17 +245,22 @@ int plan_create(mri_plan **out, int nx, int ny, int nk, int nc, const float *tra
             delete p;
             return fail(rc, form + " tensor-core path: shared-memory plan does not fit");
         }
-        if (rc == MRI_OK) rc = dev_alloc(p, &p->axT, (size_t)nx * p->nk_pad);
+        if (p->adj_tile_px == 128) {
+            if (rc == MRI_OK) rc = dev_alloc(p, &p->axP, (size_t)(p->nx_pad / 16) * p->nk_pad);
+            if (rc == MRI_OK) rc = dev_alloc(p, &p->axQ, (size_t)16 * p->nk_pad);
+        } else {
+            if (rc == MRI_OK) rc = dev_alloc(p, &p->axT, (size_t)nx * p->nk_pad);
+        }
         if (rc == MRI_OK) rc = dev_alloc(p, &p->ayT, (size_t)ny * p->nk_pad);
         if (precision == MRI_TF32) {
             if (rc == MRI_OK) rc = dev_alloc(p, &p->afwd_t, (size_t)2 * nk * p->kx);
-            if (rc == MRI_OK) rc = dev_alloc(p, &p->badj_t, (size_t)p->ny_pad * p->kk);
+            if (rc == MRI_OK) rc = dev_alloc(p, &p->badj_t, (size_t)p->badj_rows * p->kk);
             if (rc == MRI_OK) rc = dev_alloc(p, &p->bfwd_t, (size_t)nc * p->ny_pad * p->kx);
         } else {
             if (rc == MRI_OK) rc = dev_alloc(p, &p->afwd_hi, (size_t)2 * nk * p->kx);
             if (rc == MRI_OK) rc = dev_alloc(p, &p->afwd_lo, (size_t)2 * nk * p->kx);
-            if (rc == MRI_OK) rc = dev_alloc(p, &p->badj_hi, (size_t)p->ny_pad * p->kk);
-            if (rc == MRI_OK) rc = dev_alloc(p, &p->badj_lo, (size_t)p->ny_pad * p->kk);
+            if (rc == MRI_OK) rc = dev_alloc(p, &p->badj_hi, (size_t)p->badj_rows * p->kk);
+            if (rc == MRI_OK) rc = dev_alloc(p, &p->badj_lo, (size_t)p->badj_rows * p->kk);
             if (rc == MRI_OK) rc = dev_alloc(p, &p->bfwd_hi, (size_t)nc * p->ny_pad * p->kx);
             if (rc == MRI_OK) rc = dev_alloc(p, &p->bfwd_lo, (size_t)nc * p->ny_pad * p->kx);
         }
@@ -286,17 +292,19 @@ int plan_create(mri_plan **out, int nx, int ny, int nk, int nc, const float *tra
     cudaError_t e = cudaSuccess;
     if (precision == MRI_BF16X3) {
         __nv_bfloat16 *zb[] = {p->afwd_hi, p->afwd_lo, p->badj_hi, p->badj_lo, p->bfwd_hi, p->bfwd_lo};
-        size_t zn[] = {(size_t)2 * nk * p->kx, (size_t)2 * nk * p->kx, (size_t)p->ny_pad * p->kk,
-                       (size_t)p->ny_pad * p->kk, (size_t)nc * p->ny_pad * p->kx, (size_t)nc * p->ny_pad * p->kx};
+        size_t zn[] = {(size_t)2 * nk * p->kx, (size_t)2 * nk * p->kx, (size_t)p->badj_rows * p->kk,
+                       (size_t)p->badj_rows * p->kk, (size_t)nc * p->ny_pad * p->kx, (size_t)nc * p->ny_pad * p->kx};
         for (int q = 0; q < 6 && e == cudaSuccess; ++q) e = cudaMemsetAsync(zb[q], 0, zn[q] * 2, s);
     } else if (precision == MRI_TF32) {
         float *zt[] = {p->afwd_t, p->badj_t, p->bfwd_t};
-        size_t zn[] = {(size_t)2 * nk * p->kx, (size_t)p->ny_pad * p->kk, (size_t)nc * p->ny_pad * p->kx};
+        size_t zn[] = {(size_t)2 * nk * p->kx, (size_t)p->badj_rows * p->kk, (size_t)nc * p->ny_pad * p->kx};
         for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaMemsetAsync(zt[q], 0, zn[q] * 4, s);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(p->part, 0, (size_t)p->ksplit * nc * ny * p->nx_pad * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->y, 0, (size_t)nc * p->nk_pad * 8, s);
     if (e == cudaSuccess && p->axT) e = cudaMemsetAsync(p->axT, 0, (size_t)nx * p->nk_pad * 8, s);
+    if (e == cudaSuccess && p->axP) e = cudaMemsetAsync(p->axP, 0, (size_t)(p->nx_pad / 16) * p->nk_pad * 8, s);
+    if (e == cudaSuccess && p->axQ) e = cudaMemsetAsync(p->axQ, 0, (size_t)16 * p->nk_pad * 8, s);
     if (e == cudaSuccess && p->ayT) e = cudaMemsetAsync(p->ayT, 0, (size_t)ny * p->nk_pad * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->scal, 0, sizeof(DevScalars), s);
     if (e == cudaSuccess && is_tc_precision(precision)) {
@@ -335,7 +343,6 @@ MRI_API int mri_plan_set_trajectory(mri_plan *p, const float *traj, mri_stream_t
     if (!p || !traj) return fail(MRI_ERR_INVALID, "null plan or trajectory");
     cudaError_t e = launch_factors(p, traj, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "factor generation");
-    p->launches += 2;
     return MRI_OK;
 }
 
@@ -386,8 +393,9 @@ MRI_API size_t mri_plan_estimate_bytes(int nx, int ny, int nk, int nc, int preci
     if (is_tc_precision(precision)) {
         // BF16x3 hi + lo (2 + 2 bytes) and TF32 (4 bytes) operands take the same bytes
         if (tc_plan_tiling(&t) != MRI_OK) return 0;
-        bytes += c64 * ((size_t)nx * t.nk_pad + (size_t)ny * t.nk_pad);
-        bytes += bf * (2 * (size_t)2 * nk * t.kx + 2 * (size_t)t.ny_pad * t.kk + 2 * (size_t)nc * t.ny_pad * t.kx);
+        const size_t ax_rows = t.adj_tile_px == 128 ? (size_t)t.nx_pad / 16 + 16 : (size_t)nx;
+        bytes += c64 * (ax_rows * t.nk_pad + (size_t)ny * t.nk_pad);
+        bytes += bf * (2 * (size_t)2 * nk * t.kx + 2 * (size_t)t.badj_rows * t.kk + 2 * (size_t)nc * t.ny_pad * t.kx);
     } else {
         int per = 0;
         t.ksplit = choose_ksplit_fp32(&t, &per);

@@ -14,13 +14,16 @@ namespace mri {
 
 namespace {
 
-__device__ __forceinline__ float2 dft_phasor(float k, int idx, int n) {
-    const double t = (double)k * (double)(idx - n / 2);
+// exp(-i 2 pi k x) for an integer coordinate x
+__device__ __forceinline__ float2 phasor_at(float k, int x) {
+    const double t = (double)k * (double)x;
     const double f = t - rint(t);
     float s, c;
     sincospif(-2.0f * (float)f, &s, &c);
     return make_float2(c, s);
 }
+
+__device__ __forceinline__ float2 dft_phasor(float k, int idx, int n) { return phasor_at(k, idx - n / 2); }
 
 __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
@@ -42,14 +45,19 @@ __device__ __forceinline__ uint2 tf32_pair(float a, float b) { return make_uint2
 // F [nk][n] and FT [n][nk] are the FP32 factor and its transpose (either may
 // be null).  emb_hi/lo (nullable) receive the forward-product embedding
 // rows 2k: (Re, -Im), 2k+1: (Im, Re) at columns 2*idx, leading dim ld_emb.
-// cemb_hi/lo (nullable) receive the adjoint-product embedding of conj(F):
-// row idx, columns 2k, 2k+1 = (Re, -Im), leading dim ld_cemb.  emb_t and
-// cemb_t (nullable) receive the same embeddings as TF32-rounded FP32.
+// cemb_hi/lo (nullable) receive the adjoint-product embedding of
+// G = conj(F), leading dim ld_cemb: with one row per index, row idx holds
+// (Re G, Im G) at columns 2k, 2k+1; with two rows per index (cemb_two_rows)
+// row 2 idx holds (Re G, -Im G) and row 2 idx + 1 holds (Im G, Re G), the
+// right operand of [Re U | Im U] G whose output columns 2 idx, 2 idx + 1
+// are Re and Im of column idx.  emb_t and cemb_t (nullable) receive the
+// same embeddings as TF32-rounded FP32.
 __global__ void factor_tile_kernel(const float *__restrict__ traj, int axis, int n, int nk,
                                    float2 *__restrict__ F, float2 *__restrict__ FT, int ld_t,
                                    uint32_t *__restrict__ emb_hi, uint32_t *__restrict__ emb_lo,
                                    uint2 *__restrict__ emb_t, int ld_emb, uint32_t *__restrict__ cemb_hi,
-                                   uint32_t *__restrict__ cemb_lo, uint2 *__restrict__ cemb_t, int ld_cemb) {
+                                   uint32_t *__restrict__ cemb_lo, uint2 *__restrict__ cemb_t, int ld_cemb,
+                                   int cemb_two_rows) {
     __shared__ float2 tile[32][33];
     const int k0 = blockIdx.x * 32, p0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -85,16 +93,46 @@ __global__ void factor_tile_kernel(const float *__restrict__ traj, int axis, int
         if (k < nk && idx < n) {
             const float2 v = tile[tx][q];
             if (FT) FT[(size_t)idx * ld_t + k] = v;
-            if (cemb_hi) {
-                uint32_t h, l;
-                // conj(F) = (Re, -Im) at columns 2k, 2k+1
-                split_pair(v.x, -v.y, h, l);
-                cemb_hi[((size_t)idx * ld_cemb) / 2 + k] = h;
-                cemb_lo[((size_t)idx * ld_cemb) / 2 + k] = l;
+            // G = conj(F) = (v.x, -v.y)
+            if (cemb_two_rows) {
+                const size_t r0 = ((size_t)(2 * idx) * ld_cemb) / 2 + k, r1 = r0 + (size_t)ld_cemb / 2;
+                if (cemb_hi) {
+                    uint32_t h, l;
+                    split_pair(v.x, v.y, h, l);  // (Re G, -Im G)
+                    cemb_hi[r0] = h;
+                    cemb_lo[r0] = l;
+                    split_pair(-v.y, v.x, h, l);  // (Im G, Re G)
+                    cemb_hi[r1] = h;
+                    cemb_lo[r1] = l;
+                }
+                if (cemb_t) {
+                    cemb_t[r0] = tf32_pair(v.x, v.y);
+                    cemb_t[r1] = tf32_pair(-v.y, v.x);
+                }
+            } else {
+                if (cemb_hi) {
+                    uint32_t h, l;
+                    split_pair(v.x, -v.y, h, l);  // (Re G, Im G)
+                    cemb_hi[((size_t)idx * ld_cemb) / 2 + k] = h;
+                    cemb_lo[((size_t)idx * ld_cemb) / 2 + k] = l;
+                }
+                if (cemb_t) cemb_t[((size_t)idx * ld_cemb) / 2 + k] = tf32_pair(v.x, -v.y);
             }
-            if (cemb_t) cemb_t[((size_t)idx * ld_cemb) / 2 + k] = tf32_pair(v.x, -v.y);
         }
     }
+}
+
+// Phasor table of one axis: T[r][k] = exp(-i 2 pi k_k (x0 + step r)) for
+// r < rows, k < nk, leading dim ld.  The adjoint's pixel-row form takes A_x as
+// the product of two such tables (pixel i = 16 a + b: the row of 16 a - nx/2
+// times the row of b), a few FP32 roundings from the direct phasor.
+__global__ void phasor_table_kernel(const float *__restrict__ traj, int axis, int nk, int rows, int x0, int step,
+                                    float2 *__restrict__ T, int ld) {
+    const int k = blockIdx.x * 32 + threadIdx.x;
+    if (k >= nk) return;
+    const float kv = traj[2 * k + axis];
+    for (int r = blockIdx.y * blockDim.y + threadIdx.y; r < rows; r += blockDim.y * gridDim.y)
+        T[(size_t)r * ld + k] = phasor_at(kv, x0 + step * r);
 }
 
 }  // namespace
@@ -105,13 +143,23 @@ cudaError_t launch_factors(mri_plan *p, const float *traj, cudaStream_t s) {
         dim3 grid(ceil_div(p->nk, 32), ceil_div(p->nx, 32));
         factor_tile_kernel<<<grid, block, 0, s>>>(traj, 0, p->nx, p->nk, p->ax, p->axT, p->nk_pad,
                                                   (uint32_t *)p->afwd_hi, (uint32_t *)p->afwd_lo,
-                                                  (uint2 *)p->afwd_t, p->kx, nullptr, nullptr, nullptr, 0);
+                                                  (uint2 *)p->afwd_t, p->kx, nullptr, nullptr, nullptr, 0, 0);
     }
     {
         dim3 grid(ceil_div(p->nk, 32), ceil_div(p->ny, 32));
         factor_tile_kernel<<<grid, block, 0, s>>>(traj, 1, p->ny, p->nk, p->ay, p->ayT, p->nk_pad, nullptr,
                                                   nullptr, nullptr, 0, (uint32_t *)p->badj_hi,
-                                                  (uint32_t *)p->badj_lo, (uint2 *)p->badj_t, p->kk);
+                                                  (uint32_t *)p->badj_lo, (uint2 *)p->badj_t, p->kk,
+                                                  p->adj_tile_px == 128);
+    }
+    p->launches += 2;
+    if (p->axP) {
+        const int prow = p->nx_pad / 16;
+        phasor_table_kernel<<<dim3(ceil_div(p->nk, 32), ceil_div(prow, 8)), block, 0, s>>>(
+            traj, 0, p->nk, prow, -(p->nx / 2), 16, p->axP, p->nk_pad);
+        phasor_table_kernel<<<dim3(ceil_div(p->nk, 32), 2), block, 0, s>>>(traj, 0, p->nk, 16, 0, 1, p->axQ,
+                                                                           p->nk_pad);
+        p->launches += 2;
     }
     return cudaGetLastError();
 }

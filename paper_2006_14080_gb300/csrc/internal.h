@@ -74,7 +74,11 @@ struct mri_plan {
     float2 *ax = nullptr;   // [nk][nx]
     float2 *ay = nullptr;   // [nk][ny]
     // transposed FP32 factors used by the tensor-core path
-    float2 *axT = nullptr;  // [nx][nk]
+    float2 *axT = nullptr;  // [nx][nk] (adjoint row-pair form)
+    // adjoint pixel-row form: A_x[k][i] = axP[i / 16][k] * axQ[i % 16][k] with
+    // axP[a][k] = exp(-i 2 pi kx_k (16 a - nx/2)), axQ[b][k] = exp(-i 2 pi kx_k b)
+    float2 *axP = nullptr;  // [nx_pad / 16][nk_pad]
+    float2 *axQ = nullptr;  // [16][nk_pad]
     float2 *ayT = nullptr;  // [ny][nk]
 
     int nk_pad = 0;   // round_up(nk, 32): leading dimension of sample-indexed rows (axT, ayT, y)
@@ -85,21 +89,28 @@ struct mri_plan {
     int ny_pad = 0;   // round_up(ny, 16), or round_up(ny, 256) past 256: UMMA N granularity
     int nx_pad = 0;   // round_up(nx, 64): image rows per adjoint M tile group
     int fwd_coils_per_tile = 0, fwd_block_n = 0, fwd_n_tiles = 0, fwd_m_tiles = 0;
-    int adj_m_tiles = 0, adj_block_n = 0;
+    int adj_m_tiles = 0, adj_block_n = 0;  // adjoint M tiles (coils x pixel tiles) and UMMA N
+    // adjoint M tile: 64 pixels as Re/Im row pairs of the embedded U (B =
+    // conj(A_y) with one row per image column), or 128 pixels with one row
+    // each (B with two rows per column, UMMA N = 2 ny_pad; when ny <= 128
+    // and nx_pad is a multiple of 128)
+    int adj_tile_px = 64;
+    int badj_rows = 0;  // rows of the adjoint B operand: ny_pad, or 2 ny_pad with 128-pixel tiles
     int fwd_cluster = 1, adj_cluster = 1;    // CTAs per thread-block cluster (B operand multicast)
     int fwd_grid = 0, adj_grid = 0;          // persistent grid sizes (co-resident CTAs)
     __nv_bfloat16 *afwd_hi = nullptr, *afwd_lo = nullptr;  // [2*nk][kx]
-    __nv_bfloat16 *badj_hi = nullptr, *badj_lo = nullptr;  // [ny_pad][kk]
+    __nv_bfloat16 *badj_hi = nullptr, *badj_lo = nullptr;  // [badj_rows][kk]
     __nv_bfloat16 *bfwd_hi = nullptr, *bfwd_lo = nullptr;  // [nc*ny_pad][kx]
     // TF32 form: the same operands as single TF32-rounded FP32 matrices
     float *afwd_t = nullptr;  // [2*nk][kx]
-    float *badj_t = nullptr;  // [ny_pad][kk]
+    float *badj_t = nullptr;  // [badj_rows][kk]
     float *bfwd_t = nullptr;  // [nc*ny_pad][kx]
     // tensor maps of the operands; in the TF32 form the _hi and _lo maps are
     // the same map, and a K block's two 128-byte halves are its columns
     // [64 kb, 64 kb + 32) and [64 kb + 32, 64 kb + 64)
     CUtensorMap tm_afwd_hi, tm_afwd_lo, tm_bfwd_hi, tm_bfwd_lo, tm_badj_hi, tm_badj_lo;
     CUtensorMap tm_axT, tm_y, tm_ayT;  // FP32 views of axT, y, ayT for staged factor tiles
+    CUtensorMap tm_axP, tm_axQ;        // FP32 views of axP, axQ (pixel-row form)
 
     // operator workspace
     float2 *bsx = nullptr;    // [nc][nx][ny] S_c . x (FP32 path)

@@ -23,14 +23,21 @@
 //   matching 64-sample x 32-column tiles of A_y staged in shared memory by a
 //   TMA warp.
 // Adjoint: W_c = U_c conj(A_y) with U_c[i][k] = conj(A_x[k][i]) y_c[k]
-//     A  = embedded U_c          built by producer warps from A_x^H and y tiles
+//     A  = U_c                   built by producer warps from A_x^H and y tiles
 //                                that a TMA warp stages, written to tensor
 //                                memory (the UMMAs read A from TMEM)
-//     B  = conj(A_y)^T           [ny_pad][kk]      static, TMA
-//   tile: 128 rows (64 pixels of one coil) x ny_pad columns (at most 256; a
-//   wider image takes one launch per 256-column part), split over
-//   contiguous k-space ranges; the epilogue writes partial images that
-//   launch_adj_reduce sums in a fixed order (the paper's cross-core sum).
+//     B  = conj(A_y)^T           [badj_rows][kk]   static, TMA
+//   Two tile forms.  Row pairs: 128 rows = 64 pixels of one coil, U embedded
+//   as above, B one row (Re, Im) per image column, UMMA N = ny_pad (at most
+//   256; a wider image takes one launch per 256-column part).  Pixel rows
+//   (ny <= 128, nx_pad a multiple of 128): 128 rows = 128 pixels, row i of A
+//   is (Re U, Im U) along K and B carries the complex structure instead,
+//   rows 2j: (Re G, -Im G) and 2j+1: (Im G, Re G) for G = conj(A_y)[.][j],
+//   so output columns 2j, 2j+1 are Re and Im of image column j and the UMMA
+//   is 2 ny_pad wide: twice the columns per U element formed, on the wider
+//   UMMA shape.  Either way the tile is split over contiguous k-space
+//   ranges; the epilogue writes partial images that launch_adj_reduce sums
+//   in a fixed order (the paper's cross-core sum).
 //
 // Both kernels are persistent (one CTA per SM), warp-specialised, with
 // mbarrier rings between the loaders/producers and the single UMMA-issuing
@@ -55,7 +62,12 @@ constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s per wait
 constexpr uint64_t kDrainLimitNs = 200000000ull;  // 0.2 s per drain wait
 constexpr int kTileBytesA = kTcBlockM * 128;      // 128 rows x 64 bf16
 constexpr int kAyChunkBytes = 32 * 64 * 8;        // 32 columns x 64 samples, complex FP32
-constexpr int kRawBytes = 2 * 64 * 128;           // 64 pixels x 32 samples of A_x^H, complex FP32
+// one raw stage of the adjoint, 32 samples, complex FP32 in 128-byte-swizzled
+// halves of sixteen samples: row pairs, the 64 pixel rows of A_x^T (16 KB);
+// pixel rows, the 8 axP rows and 16 axQ rows whose products are the tile's
+// 128 pixel rows of A_x^T (6 KB: P half 0, P half 1, Q half 0, Q half 1)
+constexpr int raw_bytes_for(int px) { return px == 128 ? 2 * (8 + 16) * 128 : 2 * px * 128; }
+constexpr int kRawQ0 = 2 * 8 * 128;  // offset of the axQ halves in a pixel-row raw stage
 constexpr int kRawYBytes = 32 * 8;                // 32 samples of y_c
 constexpr int kFwdThreads = 224;                  // w0 TMA, w1 UMMA, w2 A_y TMA, w3-6 epilogue
 #ifndef MRI_ADJ_PRODUCER_WARPS
@@ -477,19 +489,23 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 // through shared memory.  TMEM columns: n_acc accumulators of ny_pad columns,
 // then `stages` A slots of 64 columns (BF16x3: 32 hi, 32 lo, two bf16 per
 // column; TF32: the 64 K elements, one per column) starting at a_col0.
-template <bool kTf32>
+// kPx128 selects the pixel-row tile form (128 pixels, one TMEM lane each).
+template <bool kTf32, bool kPx128>
 __global__ void __launch_bounds__(kAdjThreads, 1)
     adj_tc_kernel(const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
-                  const __grid_constant__ CUtensorMap t_axT, const __grid_constant__ CUtensorMap t_y,
-                  const AdjParams P) {
+                  const __grid_constant__ CUtensorMap t_axT, const __grid_constant__ CUtensorMap t_axQ,
+                  const __grid_constant__ CUtensorMap t_y, const AdjParams P) {
+    // t_axT: A_x^T (row pairs) or axP (pixel rows); t_axQ: axQ (pixel rows only)
     if (should_skip(P.sc, P.skip)) return;
+    constexpr int kPx = kPx128 ? 128 : 64;  // pixels per M tile
+    constexpr int kRawB = raw_bytes_for(kPx);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     const uint32_t b_bytes = (uint32_t)P.ny_pad * 128u;
     const uint32_t stage_bytes = 2u * b_bytes;  // B hi, B lo
     const int S = P.stages, R = P.raw_stages, NA = P.n_acc;
     uint8_t *raw = smem + (size_t)S * stage_bytes;
-    uint8_t *yraw = raw + (size_t)R * kRawBytes;
+    uint8_t *yraw = raw + (size_t)R * kRawB;
     uint64_t *bars = (uint64_t *)(yraw + (size_t)R * kRawYBytes);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + S);
     const uint32_t rfull0 = smem_u32(bars + 2 * S), rempty0 = smem_u32(bars + 2 * S + R);
@@ -531,6 +547,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         prefetch_tensormap(&tb_hi);
         prefetch_tensormap(&tb_lo);
         prefetch_tensormap(&t_axT);
+        if (kPx128) prefetch_tensormap(&t_axQ);
         prefetch_tensormap(&t_y);
     }
     fence_before_sync();
@@ -541,15 +558,16 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
     if (warp < kAdjProducerWarps) {
         // producers: warp w owns TMEM lanes [32 (w%4), 32 (w%4) + 32) and the
         // kSpw samples [kSpw kh, kSpw kh + kSpw) of each K block (kh = w/4).
-        // Lane l holds row r = 32 (w%4) + l of U's real embedding: pixel
-        // ii = r/2, Re row (o = 0) or Im row (o = 1).  The two threads of a
-        // pixel each form half of the warp's products and swap halves.
+        // Row pairs: lane l holds row r = 32 (w%4) + l of U's real embedding,
+        // pixel ii = r/2, Re row (o = 0) or Im row (o = 1); the two threads of
+        // a pixel each form half of the warp's products and swap halves.
+        // Pixel rows: lane l holds pixel ii = r and forms all kSpw products.
         constexpr int kSpw = 128 / kAdjProducerWarps;  // samples per warp and K block
-        constexpr int kCpt = kSpw / 4;                  // 16-byte chunks (two samples) per thread
+        constexpr int kCpt = kSpw / 4;                  // 16-byte chunks (two samples) per thread and row half
         const int q = warp & 3, kh = warp >> 2;
         const int half = (kSpw * kh) >> 4, chunk0 = ((kSpw * kh) & 15) >> 1;
         const int row = 32 * q + lane;
-        const int ii = row >> 1, o = row & 1;
+        const int ii = kPx128 ? row : row >> 1, o = kPx128 ? 0 : row & 1;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         Ring rr, rs;
         uint32_t issued_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -584,11 +602,52 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                 }
                 // staged A_x^H half-row (128-byte swizzled, sixteen samples) and
                 // y_c chunk: this thread's samples are chunks chunk0 + kCpt o + c
-                const uint8_t *arow = raw + (size_t)rr.stage * kRawBytes + half * (kRawBytes / 2) + ii * 128;
+                const uint8_t *arow = raw + (size_t)rr.stage * kRawB + (kPx128 ? half * (kRawQ0 / 2) + (ii >> 4) * 128
+                                                                               : half * (kRawB / 2) + ii * 128);
+                const uint8_t *qrow = raw + (size_t)rr.stage * kRawB + kRawQ0 + half * (kRawB - kRawQ0) / 2 +
+                                      (ii & 15) * 128;  // pixel rows only
                 const float4 *yv4 =
                     reinterpret_cast<const float4 *>(yraw + (size_t)rr.stage * kRawYBytes + half * 128);
                 const uint32_t acol = (uint32_t)(P.a_col0 + 64 * rs.stage + (kTf32 ? 2 * kSpw : kSpw) * kh);
-                if constexpr (kTf32) {
+                if constexpr (kPx128) {
+                    // this thread's kSpw samples: (Re U, Im U) in sample order, with
+                    // U = conj(P Q) y = conj(P) (conj(Q) y)
+                    uint32_t hw[kSpw], lw[kSpw];  // TF32: hw[] and lw[] are the first and second kSpw words
+#pragma unroll
+                    for (int c = 0; c < 2 * kCpt; ++c) {
+                        const int chunk = chunk0 + c;
+                        const float4 pv = *reinterpret_cast<const float4 *>(arow + ((chunk ^ ((ii >> 4) & 7)) << 4));
+                        const float4 qv = *reinterpret_cast<const float4 *>(qrow + ((chunk ^ (ii & 7)) << 4));
+                        const float4 yv = yv4[chunk];
+                        const float2 u0 = cmulc(make_float2(pv.x, pv.y),
+                                                cmulc(make_float2(qv.x, qv.y), make_float2(yv.x, yv.y)));
+                        const float2 u1 = cmulc(make_float2(pv.z, pv.w),
+                                                cmulc(make_float2(qv.z, qv.w), make_float2(yv.z, yv.w)));
+                        if constexpr (kTf32) {
+                            const uint32_t w0 = tf32_bits(u0.x), w1 = tf32_bits(u0.y);
+                            const uint32_t w2 = tf32_bits(u1.x), w3 = tf32_bits(u1.y);
+                            if (c < kCpt) {
+                                hw[4 * c] = w0;
+                                hw[4 * c + 1] = w1;
+                                hw[4 * c + 2] = w2;
+                                hw[4 * c + 3] = w3;
+                            } else {
+                                lw[4 * (c - kCpt)] = w0;
+                                lw[4 * (c - kCpt) + 1] = w1;
+                                lw[4 * (c - kCpt) + 2] = w2;
+                                lw[4 * (c - kCpt) + 3] = w3;
+                            }
+                        } else {
+                            split2(u0.x, u0.y, hw[2 * c], lw[2 * c]);
+                            split2(u1.x, u1.y, hw[2 * c + 1], lw[2 * c + 1]);
+                        }
+                    }
+                    mbar_arrive(rempty0 + 8 * rr.stage);
+                    rr.next(R);
+                    // TF32: 2 kSpw consecutive columns; BF16x3: kSpw hi columns, kSpw lo columns 32 on
+                    tmem_st_cols<kSpw>(tmem_base + lane_base + acol, hw);
+                    tmem_st_cols<kSpw>(tmem_base + lane_base + acol + (kTf32 ? kSpw : 32), lw);
+                } else if constexpr (kTf32) {
                     // this thread's 2 kCpt samples: Re-row pairs (ur, -ui) and Im-row pairs (ui, ur)
                     uint32_t rw[4 * kCpt], iw[4 * kCpt];
 #pragma unroll
@@ -736,10 +795,17 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                 for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(rempty0 + 8 * rg.stage, rg.phase ^ 1, abort_flag, kWaitLimitNs)) break;
                     const uint32_t rb = rfull0 + 8 * rg.stage;
-                    const uint32_t dst = smem_u32(raw + (size_t)rg.stage * kRawBytes);
-                    mbar_arrive_expect_tx(rb, kRawBytes + kRawYBytes);
-                    tma_load_2d(dst, &t_axT, rb, kb * 64, ib * 64);
-                    tma_load_2d(dst + kRawBytes / 2, &t_axT, rb, kb * 64 + 32, ib * 64);
+                    const uint32_t dst = smem_u32(raw + (size_t)rg.stage * kRawB);
+                    mbar_arrive_expect_tx(rb, kRawB + kRawYBytes);
+                    if constexpr (kPx128) {
+                        tma_load_2d(dst, &t_axT, rb, kb * 64, ib * 8);
+                        tma_load_2d(dst + kRawQ0 / 2, &t_axT, rb, kb * 64 + 32, ib * 8);
+                        tma_load_2d(dst + kRawQ0, &t_axQ, rb, kb * 64, 0);
+                        tma_load_2d(dst + kRawQ0 + (kRawB - kRawQ0) / 2, &t_axQ, rb, kb * 64 + 32, 0);
+                    } else {
+                        tma_load_2d(dst, &t_axT, rb, kb * 64, ib * kPx);
+                        tma_load_2d(dst + kRawB / 2, &t_axT, rb, kb * 64 + 32, ib * kPx);
+                    }
                     tma_load_2d(smem_u32(yraw + (size_t)rg.stage * kRawYBytes), &t_y, rb, kb * 64, c);
                     issued_phase[rg.stage] = rg.phase;
                     issued_mask |= 1 << rg.stage;
@@ -751,10 +817,10 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                     if (issued_mask & (1 << r)) drain_wait(rfull0 + 8 * r, issued_phase[r]);
         }
     } else {
-        // epilogue: warps 9..12; TMEM lane quadrant = warp % 4
+        // epilogue: the four warps after the UMMA warp; TMEM lane quadrant = warp % 4
         const int wq = warp & 3;
         const int row = wq * 32 + lane;
-        const int ii = row >> 1, o = row & 1;
+        const int ii = kPx128 ? row : row >> 1, o = kPx128 ? 0 : row & 1;
         const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
         int lt = 0;
         for (int g = cluster_id; g < P.num_groups; g += num_clusters, ++lt) {
@@ -765,10 +831,26 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
             fence_after_sync();
             const int p = u / P.m_tiles, m = u % P.m_tiles;
             const int c = m % P.nc, ib = m / P.nc;
-            const int i = ib * 64 + ii;
+            const int i = ib * kPx + ii;
+            const uint32_t col0 = (uint32_t)(a * P.ny_pad);
+            if constexpr (kPx128) {
+                // columns 2j, 2j+1 = Re, Im of image column j (UMMA N = 2 ny_pad, a multiple of 32)
+                float2 *dst = P.part + ((size_t)p * P.nc + c) * P.ny * P.nx_pad + i;
+                for (int jc = 0; jc < P.ny_pad; jc += 32) {
+                    float v[32];
+                    tmem_ld_32cols(tmem_base + lane_base + col0 + jc, v);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int j = jc / 2 + q;
+                        if (j < P.ny_lim) dst[(size_t)j * P.nx_pad] = make_float2(v[2 * q], v[2 * q + 1]);
+                    }
+                }
+                fence_before_sync();
+                mbar_arrive(tempty0 + 8 * a);
+                continue;
+            }
             float *dst = reinterpret_cast<float *>(P.part + ((size_t)p * P.nc + c) * P.ny * P.nx_pad) + 2 * i + o;
             const size_t jstride = 2 * (size_t)P.nx_pad;
-            const uint32_t col0 = (uint32_t)(a * P.ny_pad);
             int jc = 0;
             for (; jc + 32 <= P.ny_pad; jc += 32) {
                 float v[32];
@@ -873,9 +955,9 @@ void adj_smem_plan(const mri_plan *p, int *stages, int *raw_stages, size_t *byte
                    int *a_col0 = nullptr) {
     // shared memory holds the B (conj A_y) stages and the raw A_x^H / y ring;
     // TMEM holds the accumulators and one 64-column A slot per stage
-    const int bn = p->adj_block_n;  // UMMA N: conj(A_y) rows per tile
+    const int bn = p->adj_block_n;  // UMMA N: conj(A_y) operand rows per tile
     const int stage = 2 * bn * 128;
-    const int raw = kRawBytes + kRawYBytes;
+    const int raw = raw_bytes_for(p->adj_tile_px) + kRawYBytes;
     int s = 4, r = 0, na = 2, col0 = 0;
     for (; s >= 2; --s) {
         na = (round_up(2 * bn, 64) + 64 * s <= 512) ? 2 : 1;
@@ -889,6 +971,17 @@ void adj_smem_plan(const mri_plan *p, int *stages, int *raw_stages, size_t *byte
     *bytes = (size_t)kSmemSlack + (size_t)s * stage + (size_t)r * raw;
     if (n_acc) *n_acc = na;
     if (a_col0) *a_col0 = col0;
+}
+
+// Column parts of the adjoint, one launch each: 256-column parts of a wider
+// image in the row-pair form, always one in the pixel-row form.
+int adj_parts(const mri_plan *p) { return p->adj_tile_px == 128 ? 1 : p->ny_pad / p->adj_block_n; }
+
+// The adjoint kernel instantiation for the plan's precision and tile form.
+decltype(&adj_tc_kernel<false, false>) adj_kernel_for(const mri_plan *p) {
+    const bool w = p->adj_tile_px == 128;
+    if (p->precision == MRI_TF32) return w ? adj_tc_kernel<true, true> : adj_tc_kernel<true, false>;
+    return w ? adj_tc_kernel<false, true> : adj_tc_kernel<false, false>;
 }
 
 }  // namespace
@@ -921,7 +1014,9 @@ int tc_plan_tiling(mri_plan *p) {
     p->fwd_block_n = p->ny_pad > 256 ? 256 : p->fwd_coils_per_tile * p->ny_pad;
     p->fwd_n_tiles = ceil_div(p->nc, p->fwd_coils_per_tile);
     p->fwd_m_tiles = ceil_div(2 * p->nk, kTcBlockM);
-    // adjoint: 64 pixels (128 embedded rows) of one coil per M tile; split K
+    // adjoint: 64 pixels as 128 embedded rows, or 128 pixels as 128 rows
+    // with the complex structure in B (when the image is at most 128 columns
+    // wide and nx_pad is a multiple of 128), of one coil per M tile; split K
     // (k-space samples) so that the units fill the SMs evenly, with at most
     // kMaxKbPerSplit K blocks per split.  The tensor-core accumulation into
     // TMEM loses a roughly constant, same-signed fraction of an ulp of the
@@ -931,9 +1026,11 @@ int tc_plan_tiling(mri_plan *p) {
     // 4.8e-6 at 16, against 3.9e-6 for exact accumulation of the same BF16x3
     // products); 32 blocks keep the operator within 1e-5 for any nk at a
     // cost of 6% on that adjoint (more partial images to write and sum)
-    p->adj_m_tiles = p->nc * (p->nx_pad / 64);
-    p->adj_block_n = std::min(p->ny_pad, 256);
-    const int n_parts = p->ny_pad / p->adj_block_n;  // column parts of the image, one launch each
+    p->adj_tile_px = (p->nx_pad % 128 == 0 && p->ny_pad <= 128) ? 128 : 64;
+    p->adj_m_tiles = p->nc * (p->nx_pad / p->adj_tile_px);
+    p->adj_block_n = p->adj_tile_px == 128 ? 2 * p->ny_pad : std::min(p->ny_pad, 256);
+    p->badj_rows = p->adj_tile_px == 128 ? 2 * p->ny_pad : p->ny_pad;
+    const int n_parts = adj_parts(p);  // column parts of the image, one launch each
     const int num_kb = p->kk / kTcBlockK;
     long best_cost = -1;
     int best_split = 1;
@@ -966,8 +1063,13 @@ int tc_make_tensor_maps(mri_plan *p) {
     const uint64_t nkf = 2ull * p->nk_pad;  // floats per sample-indexed row
     bool ok = make_operand_maps(p, &p->tm_afwd_hi, &p->tm_afwd_lo, p->afwd_hi, p->afwd_lo, p->afwd_t, p->kx,
                                 2ull * p->nk, kTcBlockM) &&
-              make_map(&p->tm_axT, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->axT, nkf, p->nx, 32, 64,
-                       CU_TENSOR_MAP_SWIZZLE_128B) &&
+              (p->adj_tile_px == 128
+                   ? make_map(&p->tm_axT, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->axP, nkf, p->nx_pad / 16, 32, 8,
+                              CU_TENSOR_MAP_SWIZZLE_128B) &&
+                         make_map(&p->tm_axQ, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->axQ, nkf, 16, 32, 16,
+                                  CU_TENSOR_MAP_SWIZZLE_128B)
+                   : make_map(&p->tm_axT, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->axT, nkf, p->nx, 32, 64,
+                              CU_TENSOR_MAP_SWIZZLE_128B)) &&
               make_map(&p->tm_y, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->y, nkf, p->nc, 64, 1,
                        CU_TENSOR_MAP_SWIZZLE_NONE) &&
               make_map(&p->tm_ayT, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->ayT, nkf, p->ny, 128, 32,
@@ -980,9 +1082,7 @@ int tc_make_tensor_maps(mri_plan *p) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fwd_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(adj_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(adj_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        e = cudaFuncSetAttribute(adj_kernel_for(p), cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     if (e != cudaSuccess) {
         set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
         return MRI_ERR_CUDA;
@@ -1056,7 +1156,7 @@ int tc_set_clusters(mri_plan *p, int fwd_cm, int adj_cm) {
     bool ok = make_operand_maps(p, &p->tm_bfwd_hi, &p->tm_bfwd_lo, p->bfwd_hi, p->bfwd_lo, p->bfwd_t, p->kx,
                                 (uint64_t)p->nc * p->ny_pad, p->fwd_block_n / fwd_cm) &&
               make_operand_maps(p, &p->tm_badj_hi, &p->tm_badj_lo, p->badj_hi, p->badj_lo, p->badj_t, p->kk,
-                                p->ny_pad, p->adj_block_n / adj_cm);
+                                p->badj_rows, p->adj_block_n / adj_cm);
     if (!ok) {
         set_error("cuTensorMapEncodeTiled failed");
         return MRI_ERR_CUDA;
@@ -1071,8 +1171,7 @@ int tc_set_clusters(mri_plan *p, int fwd_cm, int adj_cm) {
     const bool t = p->precision == MRI_TF32;
     p->fwd_grid = fwd_cm * (t ? resident_clusters(fwd_tc_kernel<true>, kFwdThreads, fsm, fwd_cm, p->num_sms)
                               : resident_clusters(fwd_tc_kernel<false>, kFwdThreads, fsm, fwd_cm, p->num_sms));
-    p->adj_grid = adj_cm * (t ? resident_clusters(adj_tc_kernel<true>, kAdjThreads, asm_, adj_cm, p->num_sms)
-                              : resident_clusters(adj_tc_kernel<false>, kAdjThreads, asm_, adj_cm, p->num_sms));
+    p->adj_grid = adj_cm * resident_clusters(adj_kernel_for(p), kAdjThreads, asm_, adj_cm, p->num_sms);
     return MRI_OK;
 }
 
@@ -1126,7 +1225,7 @@ cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
     P.ny_pad = p->adj_block_n;  // the tile width
     P.nx_pad = p->nx_pad;
     P.nc = p->nc;
-    P.tiles_per_coil = p->nx_pad / 64;
+    P.tiles_per_coil = p->nx_pad / p->adj_tile_px;
     P.m_tiles = p->adj_m_tiles;
     P.kb_per_split = p->ksplit_blocks;
     P.num_kb = p->kk / kTcBlockK;
@@ -1140,19 +1239,16 @@ cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
     P.status = &p->scal->status;
     const int grid = P.cm * std::min(P.num_groups, p->adj_grid / P.cm);
     // one launch per 256-column part of the image (one launch when ny <= 256)
-    const int n_parts = p->ny_pad / p->adj_block_n;
+    const int n_parts = adj_parts(p);
     timing_begin(p, s);
     cudaError_t e = cudaSuccess;
     for (int part = 0; part < n_parts && e == cudaSuccess; ++part) {
-        const int j0 = part * p->adj_block_n;
+        const int j0 = part * p->adj_block_n;  // n_parts > 1 only in the row-pair form
         P.part = p->part + (size_t)j0 * p->nx_pad;  // column j0 of every (split, coil) plane
         P.ny_lim = p->ny - j0;
         P.b_row0 = j0;
-        e = p->precision == MRI_TF32
-                ? launch_clustered(adj_tc_kernel<true>, grid, kAdjThreads, smem, P.cm, s, p->tm_badj_hi,
-                                   p->tm_badj_lo, p->tm_axT, p->tm_y, P)
-                : launch_clustered(adj_tc_kernel<false>, grid, kAdjThreads, smem, P.cm, s, p->tm_badj_hi,
-                                   p->tm_badj_lo, p->tm_axT, p->tm_y, P);
+        e = launch_clustered(adj_kernel_for(p), grid, kAdjThreads, smem, P.cm, s, p->tm_badj_hi, p->tm_badj_lo,
+                             p->tm_axT, p->adj_tile_px == 128 ? p->tm_axQ : p->tm_axT, p->tm_y, P);
         p->launches += 1;
     }
     timing_end(p, s);

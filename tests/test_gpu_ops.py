@@ -54,7 +54,9 @@ SHAPES = [
     # nx, ny, nc, spokes, readout
     (40, 40, 3, 7, 100),      # ragged everywhere
     (64, 48, 2, 16, 128),     # non-square, ny a multiple of 16 only
-    (100, 72, 5, 9, 61),      # odd sample count
+    (100, 72, 5, 9, 61),      # odd sample count; adjoint in 128-pixel tiles (pixel-row form), rows 100-127 padding
+    (200, 96, 3, 11, 90),     # two 128-pixel adjoint tiles, the second ragged
+    (130, 128, 2, 8, 70),     # nx_pad 192: 64-pixel row-pair tiles at the pixel-row form's column limit
     (32, 32, 4, 16, 64),      # the small workload's shape
     (48, 300, 2, 5, 64),      # wider than one UMMA: two 256-column parts, the second mostly padding
     (40, 520, 1, 3, 50),      # three parts, one coil, ragged samples
