@@ -43,12 +43,11 @@ __device__ __forceinline__ float2 theta_h_theta_at(const float2 *p, int i, int j
 
 // out[i][j] = sum_c conj(S_c[i][j]) sum_p part[p][c][j][i]  (+ half_beta Theta^H Theta tv_src)
 // and optionally Re<dot_src, out> -> alpha = tau / dot.  Block (32, G),
-// G = min(nc, 16): it covers 32 consecutive pixels i of the column pair
-// (j0, j0 + 1); thread row ty takes the coils c = ty, ty + G, ..., sums each
-// coil's k-space splits for both columns (reads coalesced along i, eight in
-// flight, combined in a fixed order), applies conj(S_c) once per coil and
-// pixel, and the G groups are added in a fixed order.  Two columns per block
-// halve the grid so that it fits the GPU in one wave at the common sizes.
+// G = min(nc, 16): it covers the 64 consecutive pixels i of one column j,
+// two per lane (one 16-byte load of each partial row); thread row ty takes
+// the coils c = ty, ty + G, ..., sums each coil's k-space splits (eight
+// 16-byte loads in flight per lane, combined in a fixed order), applies conj(S_c)
+// once per coil and pixel, and the G groups are added in a fixed order.
 constexpr int kReduceGroups = 16;
 __global__ void __launch_bounds__(32 * kReduceGroups, 2)
     adj_reduce_kernel(const float2 *__restrict__ part, int ksplit, int nc, int nx, int ny, int nx_pad,
@@ -56,54 +55,51 @@ __global__ void __launch_bounds__(32 * kReduceGroups, 2)
                       float half_beta, const float2 *__restrict__ dot_src, DevScalars *sc, double *partials,
                       int skip) {
     if (should_skip(sc, skip)) return;
-    __shared__ float2 grp[kReduceGroups][2][32];
+    __shared__ float4 grp[kReduceGroups][32];
     __shared__ double red[32];
     const int tx = threadIdx.x, ty = threadIdx.y, G = blockDim.y;
-    const int i = blockIdx.x * 32 + tx, j0 = blockIdx.y * 2;
-    const bool has1 = j0 + 1 < ny;
+    const int i0 = blockIdx.x * 64 + 2 * tx, j = blockIdx.y;
+    const bool has1 = i0 + 1 < nx;  // i0 + 1 < nx_pad always (nx_pad is a multiple of 64)
     const size_t npix = (size_t)nx * ny;
-    float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
-    if (i < nx) {
-        const size_t pstride = (size_t)nc * ny * nx_pad;  // between k-space splits
-        const int off1 = has1 ? nx_pad : 0;                // column j0 + 1 (re-read j0 at the last odd column)
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i0 < nx) {
+        const size_t pstride = (size_t)nc * ny * nx_pad / 2;  // float4 units between k-space splits
         for (int c = ty; c < nc; c += G) {
-            const float2 *src = part + ((size_t)c * ny + j0) * nx_pad + i;
-            float2 w0[4], w1[4];
+            const float4 *src = reinterpret_cast<const float4 *>(part + ((size_t)c * ny + j) * nx_pad + i0);
+            // w[e] sums the splits p = e (mod 4) in increasing order
+            float4 w[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) w0[e] = w1[e] = make_float2(0.f, 0.f);
+            for (int e = 0; e < 4; ++e) w[e] = make_float4(0.f, 0.f, 0.f, 0.f);
             int p = 0;
-            for (; p + 3 < ksplit; p += 4) {
+            for (; p + 7 < ksplit; p += 8) {
+                float4 v[8];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float2 *q = src + (size_t)(p + e) * pstride;
-                    w0[e] = cadd(w0[e], q[0]);
-                    w1[e] = cadd(w1[e], q[off1]);
-                }
+                for (int e = 0; e < 8; ++e) v[e] = src[(size_t)(p + e) * pstride];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) w[e] = f4add(f4add(w[e], v[e]), v[e + 4]);
             }
-            for (; p < ksplit; ++p) {
-                const float2 *q = src + (size_t)p * pstride;
-                w0[0] = cadd(w0[0], q[0]);
-                w1[0] = cadd(w1[0], q[off1]);
-            }
-            const float2 *s = maps + c * npix + (size_t)i * ny + j0;
-            acc0 = cadd(acc0, cmulc(s[0], cadd(cadd(w0[0], w0[1]), cadd(w0[2], w0[3]))));
-            if (has1) acc1 = cadd(acc1, cmulc(s[1], cadd(cadd(w1[0], w1[1]), cadd(w1[2], w1[3]))));
+            for (; p < ksplit; ++p) w[p & 3] = f4add(w[p & 3], src[(size_t)p * pstride]);
+            const float4 t = f4add(f4add(w[0], w[1]), f4add(w[2], w[3]));
+            const float2 *s = maps + c * npix + (size_t)i0 * ny + j;
+            const float2 a0 = cmulc(s[0], make_float2(t.x, t.y));
+            const float2 a1 = has1 ? cmulc(s[ny], make_float2(t.z, t.w)) : make_float2(0.f, 0.f);
+            acc = f4add(acc, make_float4(a0.x, a0.y, a1.x, a1.y));
         }
     }
-    grp[ty][0][tx] = acc0;
-    grp[ty][1][tx] = acc1;
+    grp[ty][tx] = acc;
     __syncthreads();
     double dot = 0.0;
-    // rows 0 and 1 finish columns j0 and j0 + 1 (row 0 both when G = 1)
-    for (int col = ty; col < 2; col += G) {
-        if (i >= nx || (col == 1 && !has1)) continue;
-        const int j = j0 + col;
-        float2 v = grp[0][col][tx];
-        for (int g = 1; g < G; ++g) v = cadd(v, grp[g][col][tx]);
+    // rows 0 and 1 finish pixels i0 and i0 + 1 (row 0 both when G = 1)
+    for (int h = ty; h < 2; h += G) {
+        const int i = i0 + h;
+        if (i >= nx) continue;
+        float4 g = grp[0][tx];
+        for (int q = 1; q < G; ++q) g = f4add(g, grp[q][tx]);
+        float2 v = h ? make_float2(g.z, g.w) : make_float2(g.x, g.y);
         if (tv_src) {
-            const float2 t = theta_h_theta_at(tv_src, i, j, nx, ny);
-            v.x = fmaf(half_beta, t.x, v.x);
-            v.y = fmaf(half_beta, t.y, v.y);
+            const float2 tt = theta_h_theta_at(tv_src, i, j, nx, ny);
+            v.x = fmaf(half_beta, tt.x, v.x);
+            v.y = fmaf(half_beta, tt.y, v.y);
         }
         out[(size_t)i * ny + j] = v;
         if (dot_src) {
@@ -112,8 +108,8 @@ __global__ void __launch_bounds__(32 * kReduceGroups, 2)
         }
     }
     if (dot_src) {
-        double s = block_sum(dot, red);
-        double part_s[1] = {s};
+        double sum = block_sum(dot, red);
+        double part_s[1] = {sum};
         grid_reduce_last<1>(part_s, partials, &sc->counters[kCntDot],
                             [&](const double *tot) { sc->alpha = sc->tau / tot[0]; });
     }
@@ -319,7 +315,7 @@ int ew_blocks(int n) { return max(1, min(kEwMaxBlocks, ceil_div(n, kEwThreads)))
 
 cudaError_t launch_adj_reduce(mri_plan *p, const float2 *maps, float2 *out, const ReduceEpilogue &e,
                               cudaStream_t s) {
-    dim3 grid(ceil_div(p->nx, 32), ceil_div(p->ny, 2));
+    dim3 grid(ceil_div(p->nx, 64), p->ny);
     adj_reduce_kernel<<<grid, dim3(32, std::min(p->nc, kReduceGroups)), 0, s>>>(p->part, p->ksplit, p->nc, p->nx, p->ny, p->nx_pad, maps, out,
                                                    e.tv_src, e.half_beta, e.dot_src, p->scal, p->partials, e.skip);
     return cudaGetLastError();
