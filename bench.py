@@ -288,9 +288,8 @@ def run_gpu(args, rank, world, local_rank):
     results = {}
     out = torch.empty((p.nx, p.ny), dtype=torch.complex64, device=dev)
     with mr.Plan(p.nx, p.ny, p.nc, traj, "bf16x3") as plan:
-        if args.clusters:  # fixed schedule (e.g. to profile the configuration a tuned run chose)
-            fc, ac = (int(v) for v in args.clusters.split(","))
-            plan.set_clusters(fc, ac)
+        if args.tiles:  # fixed schedule (e.g. to profile the configuration a tuned run chose)
+            plan.set_tiles(*(int(v) for v in args.tiles.split(",")))
             tuned = plan.config()
         else:
             tuned = plan.autotune(repeats=5)  # set-up, outside the timed region
@@ -768,8 +767,9 @@ def main():
                     help="requests per wave at the rates after the first (0: all)")
     ap.add_argument("--serve-fp32-requests", type=int, default=24,
                     help="requests per wave for the FP32 form (about 2 s per request)")
-    ap.add_argument("--clusters", default="",
-                    help="'F,A': forward and adjoint cluster sizes instead of autotuning them")
+    ap.add_argument("--tiles", default="",
+                    help="'C,F,A': coils per forward tile, forward stages and adjoint stages instead of "
+                         "autotuning them")
     ap.add_argument("--forms", default="",
                     help="comma list of what to run: bf16x3 (always), e2e (host-buffer run), fp32 (plain FP32 "
                          "form), tf32 (TF32 tensor-core form); default all four for n128, all but fp32 for "

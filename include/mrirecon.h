@@ -246,13 +246,12 @@ MRI_API long long mri_batch_launch_count(const mri_batch *batch);
  * the plan's (mri_plan_estimate_bytes, unless an idle cached plan of the
  * same key exists) plus its k-space, maps, trajectory and image buffers --
  * fit under `hbm_budget_bytes` together with everything resident; idle
- * cached plans are evicted least-recently-used to make room (eviction
- * synchronises the device).  A request whose bytes exceed the whole budget
+ * cached plans are evicted least-recently-used to make room.  A request whose bytes exceed the whole budget
  * fails with MRI_ERR_NOMEM; one whose shape the precision does not support
  * fails with MRI_ERR_NOMEM too (estimate 0).  Every request runs Alg. 4
  * with its own plan and buffers, so its image is bit-identical to the one
  * mri_admm_reconstruct produces for it alone with a plan of the same
- * precision and cluster sizes, whatever else is in flight.
+ * precision, whatever else is in flight.
  * ------------------------------------------------------------------------- */
 
 typedef struct mri_server mri_server;
@@ -315,8 +314,10 @@ MRI_API int mri_server_destroy(mri_server *server);
  *   - all calls on a device share the buffer and it keeps the last call's
  *     contents; calls that overlap on the GPU (unordered streams) race on
  *     it, so serialise them.
+ *   - nc must not exceed 65535, else MRI_ERR_INVALID.
  *   - the first call on a device looks up the buffer's address; make it
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for the life of the
+ *     process: calls after a cudaDeviceReset of that device are not supported.
  * ------------------------------------------------------------------------- */
 MRI_API int mri_nudft_adjoint_noalloc(int nx, int ny, int nk, int nc, const float *traj, const mri_c64 *kspace,
                                       const mri_c64 *coil_maps, mri_c64 *image, mri_stream_t stream);
@@ -350,19 +351,25 @@ MRI_API int mri_plan_selftest_wait(mri_plan *plan, double limit_ms, mri_stream_t
 
 /* ---------------------------------------------------------------------------
  * Scheduling of the tensor-core products (not in the paper).  The forward
- * and adjoint kernels run as clusters of 1, 2, 4 or 8 CTAs that share (TMA
- * multicast) the operand common to their tiles.  The cluster size changes
- * the schedule only, never the arithmetic or its order.
+ * and adjoint kernels are persistent (one CTA per SM); their tile
+ * configuration is the number of coils per forward N tile (the UMMA N is
+ * coils x ny_pad, at most 256) and the number of operand stages of each
+ * product's shared-memory ring (2..4, as shared memory and tensor memory
+ * allow).  It changes the schedule only, never the arithmetic or its order.
+ * Every CTA loads its own operand tiles (no cluster multicast).
  * ------------------------------------------------------------------------- */
 
-/* Current configuration (nullable outputs): cluster sizes, number of
- * k-space splits of the adjoint, coils per forward tile. */
-MRI_API int mri_plan_get_config(const mri_plan *plan, int *fwd_cluster, int *adj_cluster, int *adj_ksplit,
-                                int *fwd_coils_per_tile);
+/* Current configuration (nullable outputs): coils per forward tile, forward
+ * and adjoint operand stages, number of k-space splits of the adjoint (set
+ * by the shape and SM count, not tunable: it fixes the summation order). */
+MRI_API int mri_plan_get_config(const mri_plan *plan, int *fwd_coils_per_tile, int *fwd_stages, int *adj_stages,
+                                int *adj_ksplit);
 
-/* Set the cluster sizes (0 keeps the current one); MRI_ERR_INVALID when a
- * size does not divide the tile shape; MRI_ERR_UNSUPPORTED on an FP32 plan. */
-MRI_API int mri_plan_set_clusters(mri_plan *plan, int fwd_cluster, int adj_cluster);
+/* Set the tile configuration (0 keeps the current value): coils per forward
+ * tile in 1..min(4, nc, 256 / ny_pad), stage counts in 2..4.  MRI_ERR_INVALID
+ * when the shape or the on-chip memory does not allow it; MRI_ERR_UNSUPPORTED
+ * on an FP32 plan. */
+MRI_API int mri_plan_set_tiles(mri_plan *plan, int fwd_coils_per_tile, int fwd_stages, int adj_stages);
 
 /* mri_admm_reconstruct captures its whole launch sequence into a CUDA graph
  * on first use and replays it while the stream is not the legacy default
@@ -372,22 +379,24 @@ MRI_API int mri_plan_set_clusters(mri_plan *plan, int fwd_cluster, int adj_clust
  * replays). */
 MRI_API int mri_plan_set_graphs(mri_plan *plan, int enable);
 
-/* Autotuner: time every valid cluster size of both products on this plan's
- * shape (`repeats` launches each, default 3) and keep the fastest.  The
+/* Autotuner: time every valid tile configuration of both products on this
+ * plan's shape (forward: coils per tile x stages; adjoint: stages;
+ * `repeats` launches each, default 3) and keep the fastest.  The
  * choice is also recorded in the process-wide tuning table (below), keyed by
  * precision, shape and SM count.  Synchronises `stream`; allocates a
  * temporary buffer.  No-op for FP32 plans. */
 MRI_API int mri_plan_autotune(mri_plan *plan, int repeats, mri_stream_t stream);
 
 /* Persistent tuning table.  Plans created for a (precision, nx, ny, nk, nc,
- * SM count) that the table holds start with its cluster sizes.
+ * SM count) that the table holds start with its tile configuration.
  *   mri_tuning_save: write the table to `path` as JSON
  *     {"format": "mrirecon-tuning", "version": 1, "entries": [{"precision",
- *      "nx", "ny", "nk", "nc", "sms", "fwd_cluster", "adj_cluster"}, ...]}
+ *      "nx", "ny", "nk", "nc", "sms", "fwd_coils_per_tile", "fwd_stages",
+ *      "adj_stages"}, ...]}
  *   mri_tuning_load: merge such a file into the table (MRI_ERR_INVALID, and
  *     no change, for a file that is missing, not a tuning file, or has an
- *     entry without one of those integer keys or with a cluster size other
- *     than 1, 2, 4, 8)
+ *     entry without one of those integer keys, with coils per tile outside
+ *     1..4 or a stage count outside 2..4)
  *   mri_tuning_clear / mri_tuning_count: empty the table / its entry count.
  * No GPU is needed; the table is guarded for use from several threads. */
 MRI_API int mri_tuning_save(const char *path);

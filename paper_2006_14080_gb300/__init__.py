@@ -103,7 +103,7 @@ def load(path: str = LIB_PATH):
         "mri_plan_launch_count": ([P], ctypes.c_longlong),
         "mri_plan_selftest_wait": ([P, D, P], I),
         "mri_plan_get_config": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
-        "mri_plan_set_clusters": ([P, I, I], I),
+        "mri_plan_set_tiles": ([P, I, I, I], I),
         "mri_plan_autotune": ([P, I, P], I),
         "mri_plan_set_graphs": ([P, I], I),
         "mri_batch_create": ([ctypes.POINTER(P)], I),
@@ -209,18 +209,19 @@ class Plan:
     def config(self) -> dict:
         v = [ctypes.c_int() for _ in range(4)]
         _check(load().mri_plan_get_config(self.handle, *[ctypes.byref(q) for q in v]))
-        return {"fwd_cluster": v[0].value, "adj_cluster": v[1].value, "adj_ksplit": v[2].value,
-                "fwd_coils_per_tile": v[3].value}
+        return {"fwd_coils_per_tile": v[0].value, "fwd_stages": v[1].value, "adj_stages": v[2].value,
+                "adj_ksplit": v[3].value}
 
     def set_graphs(self, enable: bool = True):
         """Capture/replay whole reconstructions as CUDA graphs (default on)."""
         _check(load().mri_plan_set_graphs(self.handle, int(bool(enable))))
 
-    def set_clusters(self, fwd: int = 0, adj: int = 0):
-        _check(load().mri_plan_set_clusters(self.handle, int(fwd), int(adj)))
+    def set_tiles(self, fwd_coils_per_tile: int = 0, fwd_stages: int = 0, adj_stages: int = 0):
+        """Tile configuration of the tensor-core products (0 keeps the current value)."""
+        _check(load().mri_plan_set_tiles(self.handle, int(fwd_coils_per_tile), int(fwd_stages), int(adj_stages)))
 
     def autotune(self, repeats: int = 3, stream=None) -> dict:
-        """Time the valid cluster sizes of both products on this shape and keep the fastest."""
+        """Time the valid tile configurations of both products on this shape and keep the fastest."""
         _check(load().mri_plan_autotune(self.handle, int(repeats), _stream(stream)))
         return self.config()
 

@@ -309,10 +309,10 @@ int plan_create(mri_plan **out, int nx, int ny, int nk, int nc, const float *tra
     if (e == cudaSuccess) e = cudaMemsetAsync(p->scal, 0, sizeof(DevScalars), s);
     if (e == cudaSuccess && is_tc_precision(precision)) {
         rc = tc_make_tensor_maps(p);
-        int fc = 0, ac = 0;
-        // cluster sizes an earlier autotune chose for this shape, if valid here
-        if (rc == MRI_OK && tuning_lookup(p, &fc, &ac) && tc_cluster_valid_fwd(p, fc) && tc_cluster_valid_adj(p, ac))
-            rc = tc_set_clusters(p, fc, ac);
+        int cpt = 0, fs = 0, as = 0;
+        // the tile configuration an earlier autotune chose for this shape, if valid here
+        if (rc == MRI_OK && tuning_lookup(p, &cpt, &fs, &as) && tc_tiles_valid(p, cpt, fs, as))
+            rc = tc_set_tiles(p, cpt, fs, as);
         if (rc != MRI_OK) {
             free_plan(p);
             return rc;
@@ -650,28 +650,29 @@ MRI_API int mri_plan_read_timing(mri_plan *p, double *fwd_ms, long long *fwd_lau
 
 MRI_API long long mri_plan_launch_count(const mri_plan *p) { return p ? p->launches : 0; }
 
-MRI_API int mri_plan_get_config(const mri_plan *p, int *fwd_cluster, int *adj_cluster, int *adj_ksplit,
-                                int *fwd_coils_per_tile) {
+MRI_API int mri_plan_get_config(const mri_plan *p, int *fwd_coils_per_tile, int *fwd_stages, int *adj_stages,
+                                int *adj_ksplit) {
     if (!p) return fail(MRI_ERR_INVALID, "null plan");
-    if (fwd_cluster) *fwd_cluster = p->fwd_cluster;
-    if (adj_cluster) *adj_cluster = p->adj_cluster;
-    if (adj_ksplit) *adj_ksplit = p->ksplit;
     if (fwd_coils_per_tile) *fwd_coils_per_tile = p->fwd_coils_per_tile;
+    if (fwd_stages) *fwd_stages = p->fwd_stages;
+    if (adj_stages) *adj_stages = p->adj_stages;
+    if (adj_ksplit) *adj_ksplit = p->ksplit;
     return MRI_OK;
 }
 
-MRI_API int mri_plan_set_clusters(mri_plan *p, int fwd_cluster, int adj_cluster) {
+MRI_API int mri_plan_set_tiles(mri_plan *p, int fwd_coils_per_tile, int fwd_stages, int adj_stages) {
     if (!p) return fail(MRI_ERR_INVALID, "null plan");
     if (!is_tc_precision(p->precision))
-        return fail(MRI_ERR_UNSUPPORTED, "cluster sizes apply to the tensor-core forms");
-    return tc_set_clusters(p, fwd_cluster, adj_cluster);
+        return fail(MRI_ERR_UNSUPPORTED, "tile configurations apply to the tensor-core forms");
+    return tc_set_tiles(p, fwd_coils_per_tile, fwd_stages, adj_stages);
 }
 
-// Times every valid cluster size of the two product kernels on this plan's
-// shape (the data do not change the work, so the plan's zeroed workspace is
-// used) and keeps the fastest.  The choice changes scheduling only, never the
-// arithmetic or its order.  Allocates a temporary coil-map buffer and
-// synchronises the stream.
+// Times every valid tile configuration of the two product kernels on this
+// plan's shape (the data do not change the work, so the plan's zeroed
+// workspace is used) and keeps the fastest: coils per forward N tile with
+// the forward stage count, and the adjoint stage count.  The choice changes
+// scheduling only, never the arithmetic or its order.  Allocates a temporary
+// coil-map buffer and synchronises the stream.
 MRI_API int mri_plan_autotune(mri_plan *p, int repeats, mri_stream_t stream) {
     if (!p) return fail(MRI_ERR_INVALID, "null plan");
     if (!is_tc_precision(p->precision)) return MRI_OK;  // the FP32 form has nothing to tune
@@ -689,41 +690,46 @@ MRI_API int mri_plan_autotune(mri_plan *p, int repeats, mri_stream_t stream) {
     cudaEventCreate(&e1);
     const bool was_timing = p->timing;
     p->timing = false;
-    int best_f = p->fwd_cluster, best_a = p->adj_cluster;
+    int best_cpt = p->fwd_coils_per_tile, best_fs = p->fwd_stages, best_as = p->adj_stages;
     float best_tf = 1e30f, best_ta = 1e30f;
     int rc = MRI_OK;
-    const int cands[] = {1, 2, 4, 8};
+    // which = 0: forward (coils per tile x stages); which = 1: adjoint (stages)
     for (int which = 0; which < 2 && rc == MRI_OK; ++which) {
-        for (int cm : cands) {
-            const bool valid = which == 0 ? tc_cluster_valid_fwd(p, cm) : tc_cluster_valid_adj(p, cm);
-            if (!valid) continue;
-            rc = which == 0 ? tc_set_clusters(p, cm, best_a) : tc_set_clusters(p, best_f, cm);
-            if (rc != MRI_OK) break;
-            cudaError_t e = cudaSuccess;
-            for (int it = 0; it <= repeats && e == cudaSuccess; ++it) {
-                if (it == 1) cudaEventRecord(e0, s);
-                e = which == 0 ? launch_fwd_tc(p, p->x, maps, p->y, p->nk_pad, kSkipNever, s)
-                               : launch_adj_tc(p, kSkipNever, s);
-            }
-            cudaEventRecord(e1, s);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                rc = cuda_fail(e, "autotune");
-                break;
-            }
-            if (which == 0 && ms < best_tf) {
-                best_tf = ms;
-                best_f = cm;
-            }
-            if (which == 1 && ms < best_ta) {
-                best_ta = ms;
-                best_a = cm;
+        const int cpt_max = which == 0 ? tc_max_coils_per_tile(p) : 1;
+        for (int cpt = 1; cpt <= cpt_max && rc == MRI_OK; ++cpt) {
+            for (int st = 2; st <= 4; ++st) {
+                const int c = which == 0 ? cpt : best_cpt, fs = which == 0 ? st : best_fs;
+                const int as = which == 0 ? best_as : st;
+                if (!tc_tiles_valid(p, c, fs, as)) continue;
+                rc = tc_set_tiles(p, c, fs, as);
+                if (rc != MRI_OK) break;
+                cudaError_t e = cudaSuccess;
+                for (int it = 0; it <= repeats && e == cudaSuccess; ++it) {
+                    if (it == 1) cudaEventRecord(e0, s);
+                    e = which == 0 ? launch_fwd_tc(p, p->x, maps, p->y, p->nk_pad, kSkipNever, s)
+                                   : launch_adj_tc(p, kSkipNever, s);
+                }
+                cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(e, "autotune");
+                    break;
+                }
+                if (which == 0 && ms < best_tf) {
+                    best_tf = ms;
+                    best_cpt = cpt;
+                    best_fs = st;
+                }
+                if (which == 1 && ms < best_ta) {
+                    best_ta = ms;
+                    best_as = st;
+                }
             }
         }
     }
-    if (rc == MRI_OK) rc = tc_set_clusters(p, best_f, best_a);
+    if (rc == MRI_OK) rc = tc_set_tiles(p, best_cpt, best_fs, best_as);
     if (rc == MRI_OK) tuning_record(p);
     p->timing = was_timing;
     cudaEventDestroy(e0);

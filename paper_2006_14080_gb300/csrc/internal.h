@@ -96,7 +96,7 @@ struct mri_plan {
     // and nx_pad is a multiple of 128)
     int adj_tile_px = 64;
     int badj_rows = 0;  // rows of the adjoint B operand: ny_pad, or 2 ny_pad with 128-pixel tiles
-    int fwd_cluster = 1, adj_cluster = 1;    // CTAs per thread-block cluster (B operand multicast)
+    int fwd_stages = 0, adj_stages = 0;      // operand ring stages of the two products (0: as many as fit)
     int fwd_grid = 0, adj_grid = 0;          // persistent grid sizes (co-resident CTAs)
     __nv_bfloat16 *afwd_hi = nullptr, *afwd_lo = nullptr;  // [2*nk][kx]
     __nv_bfloat16 *badj_hi = nullptr, *badj_lo = nullptr;  // [badj_rows][kk]
@@ -170,10 +170,11 @@ int plan_create(mri_plan **out, int nx, int ny, int nk, int nc, const float *tra
 void plan_destroy_async(mri_plan *p, cudaStream_t s);
 // Drop the cached reconstruction graph (its kernels' arguments are stale).
 void invalidate_graph(mri_plan *p);
-// Persistent autotuning table (tuning.cu): record a plan's cluster sizes /
-// look up the sizes recorded for its precision, shape and SM count.
+// Persistent autotuning table (tuning.cu): record a plan's tile configuration
+// (forward coils per tile, forward and adjoint stages) / look up the one
+// recorded for its precision, shape and SM count.
 void tuning_record(const mri_plan *p);
-bool tuning_lookup(const mri_plan *p, int *fwd_cluster, int *adj_cluster);
+bool tuning_lookup(const mri_plan *p, int *fwd_coils_per_tile, int *fwd_stages, int *adj_stages);
 // Argument checks of mri_admm_reconstruct (MRI_* status, sets the error text).
 int check_admm_args(const mri_plan *p, const mri_c64 *kspace, const mri_c64 *maps, const mri_admm_params *prm,
                     const mri_c64 *image_out);
@@ -213,11 +214,13 @@ cudaError_t launch_adj_fp32(mri_plan *p, int skip, cudaStream_t s);
 bool tc_supported(const mri_plan *p, std::string *why);
 int tc_plan_tiling(mri_plan *p);       // tile shapes and k-space splits; MRI_* status
 int tc_make_tensor_maps(mri_plan *p);  // TMA descriptors of the allocated operands; MRI_* status
-// Cluster sizes of the forward and adjoint products (1, 2, 4 or 8 where the
-// shape allows; 0 keeps the current one).  Rebuilds the tensor maps.
-int tc_set_clusters(mri_plan *p, int fwd_cm, int adj_cm);
-bool tc_cluster_valid_fwd(const mri_plan *p, int cm);
-bool tc_cluster_valid_adj(const mri_plan *p, int cm);
+// Tile configuration of the two products: coils per forward N tile
+// (1..tc_max_coils_per_tile) and operand ring stages of each (2..4, as the
+// shared memory and TMEM allow); 0 keeps the current value.  Rebuilds the
+// tensor maps.  None of them changes the arithmetic or its order.
+int tc_set_tiles(mri_plan *p, int fwd_coils_per_tile, int fwd_stages, int adj_stages);
+bool tc_tiles_valid(const mri_plan *p, int fwd_coils_per_tile, int fwd_stages, int adj_stages);
+int tc_max_coils_per_tile(const mri_plan *p);
 cudaError_t launch_fwd_tc(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace, int ld,
                           int skip, cudaStream_t s);
 cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s);

@@ -88,9 +88,8 @@ constexpr int kMaxCoilsPerTile = 4;
 #endif
 constexpr int kMaxKbPerSplit = MRI_ADJ_MAX_KB_PER_SPLIT;  // adjoint: K blocks (32 samples each) per k-space split
 
-// Work split of both kernels: clusters of `cm` CTAs process groups of cm
-// tiles (units) in lockstep; the operand shared by the group (B) is loaded
-// once, each CTA fetching 1/cm of its rows and multicasting them to all.
+// Work split of both kernels: the persistent CTAs take the tiles (units) in
+// turn, CTA b units b, b + gridDim.x, ...; every CTA loads its own operands.
 struct FwdParams {
     float2 *y;  // [nc][y_ld]
     int y_ld, nk, ny_pad, nc, cpt, block_n, n_tiles, num_kb, stages, ay_stages;
@@ -99,7 +98,7 @@ struct FwdParams {
     // sums the epilogue adds before it writes y; otherwise n_parts = 1 and
     // pw = ny_pad (the whole coil, cpt coils per tile)
     int n_parts, pw;
-    int cm, num_groups;  // cluster size; groups = ceil(m_tiles / cm) * n_tiles
+    int num_units;  // m_tiles * n_tiles
     uint32_t tmem_cols;
     const DevScalars *sc;
     int skip;
@@ -114,15 +113,13 @@ struct AdjParams {
     // the number of its columns that lie inside the image.
     int nx, ny, ny_pad, nx_pad, nc, tiles_per_coil, m_tiles, kb_per_split, num_kb, ny_lim, b_row0;
     int stages, raw_stages;
-    int n_acc, a_col0;   // accumulator buffers in TMEM; first TMEM column of the A slots
-    int cm, num_groups;  // cluster size; groups = m_tiles * ksplit / cm
+    int n_acc, a_col0;  // accumulator buffers in TMEM; first TMEM column of the A slots
+    int num_units;      // m_tiles * ksplit
     uint32_t tmem_cols;
     const DevScalars *sc;
     int skip;
     int *status;
 };
-
-__device__ __forceinline__ uint16_t cluster_mask(int cm) { return (uint16_t)((1u << cm) - 1u); }
 
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
     return (uint8_t *)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
@@ -230,15 +227,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_jc = (P.pw + 31) / 32;  // A_y chunks of 32 columns per sub-tile
-    const int rank = (int)cluster_ctarank();
-    const int cluster_id = blockIdx.x / P.cm, num_clusters = gridDim.x / P.cm;
-    const uint32_t b_slice = b_bytes / (uint32_t)P.cm;  // rows block_n / cm
-    const uint16_t mask = cluster_mask(P.cm);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, P.cm);  // released by the UMMA commits of every CTA of the cluster
+            mbar_init(empty0 + 8 * s, 1);  // released by the UMMA commit
         }
         for (int r = 0; r < R; ++r) {
             mbar_init(yfull0 + 8 * r, 1);
@@ -264,21 +257,21 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         prefetch_tensormap(&t_ay);
     }
     fence_before_sync();
-    cluster_sync();  // barriers of every CTA of the cluster are initialised before any multicast
+    __syncthreads();  // barriers initialised and TMEM allocated before any role starts
     fence_after_sync();
     const uint32_t tmem_base = *tmem_slot;
 
     if (warp == 0) {
-        // operand loader: own A tile, 1/cm of the shared B rows multicast to the cluster
+        // operand loader: the unit's A tile and B rows
         if (lane == 0) {
             Ring rg;
             uint32_t issued_phase[4] = {0, 0, 0, 0};
             int issued_mask = 0;
-            for (int g = cluster_id; g < P.num_groups && !*abort_flag; g += num_clusters) {
-                const int m_blk = (g / P.n_tiles) * P.cm + rank, n_blk = g % P.n_tiles;
+            for (int g = blockIdx.x; g < P.num_units && !*abort_flag; g += gridDim.x) {
+                const int m_blk = g / P.n_tiles, n_blk = g % P.n_tiles;
                 for (int part = 0; part < P.n_parts; ++part)
                 for (int kb = 0; kb < P.num_kb; ++kb) {
-                    const int b_row = n_blk * P.cpt * P.ny_pad + part * P.pw + rank * (P.block_n / P.cm);
+                    const int b_row = n_blk * P.cpt * P.ny_pad + part * P.pw;
                     if (!mbar_wait(empty0 + 8 * rg.stage, rg.phase ^ 1, abort_flag, kWaitLimitNs)) break;
                     const uint32_t sbase = smem_u32(smem + (size_t)rg.stage * stage_bytes);
                     const uint32_t fb = full0 + 8 * rg.stage;
@@ -287,14 +280,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                     const int x0 = kb * kTcBlockK, x1 = x0 + (kTf32 ? kTcBlockK / 2 : 0);
                     tma_load_2d(sbase, &ta_hi, fb, x0, m_blk * kTcBlockM);
                     tma_load_2d(sbase + kTileBytesA, &ta_lo, fb, x1, m_blk * kTcBlockM);
-                    const uint32_t bh = sbase + 2 * kTileBytesA + rank * b_slice;
-                    if (P.cm > 1) {
-                        tma_load_2d_multicast(bh, &tb_hi, fb, x0, b_row, mask);
-                        tma_load_2d_multicast(bh + b_bytes, &tb_lo, fb, x1, b_row, mask);
-                    } else {
-                        tma_load_2d(bh, &tb_hi, fb, x0, b_row);
-                        tma_load_2d(bh + b_bytes, &tb_lo, fb, x1, b_row);
-                    }
+                    const uint32_t bh = sbase + 2 * kTileBytesA;
+                    tma_load_2d(bh, &tb_hi, fb, x0, b_row);
+                    tma_load_2d(bh + b_bytes, &tb_lo, fb, x1, b_row);
                     issued_phase[rg.stage] = rg.phase;
                     issued_mask |= 1 << rg.stage;
                     rg.next(S);
@@ -311,9 +299,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             Ring rg;
             int lt = 0;
             bool issued_any = false;
-            // one accumulator per (group, sub-tile), in the loader's order
+            // one accumulator per (unit, sub-tile), in the loader's order
             for (int t = 0;; ++t, ++lt) {
-                if (cluster_id + (t / P.n_parts) * num_clusters >= P.num_groups) break;
+                if ((int)blockIdx.x + (t / P.n_parts) * (int)gridDim.x >= P.num_units) break;
                 const int a = lt & 1;
                 const uint32_t ap = (lt >> 1) & 1;
                 if (!mbar_wait(tempty0 + 8 * a, ap ^ 1, abort_flag, kWaitLimitNs)) break;
@@ -351,18 +339,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                         }
                     }
                     issued_any = true;
-                    // the stage is free only when every CTA of the cluster has consumed it
-                    if (P.cm > 1)
-                        umma_commit_multicast(empty0 + 8 * rg.stage, mask);
-                    else
-                        umma_commit(empty0 + 8 * rg.stage);
+                    umma_commit(empty0 + 8 * rg.stage);  // the stage is free once these UMMAs completed
                     rg.next(S);
                 }
                 if (!ok) break;
                 umma_commit(tfull0 + 8 * a);
             }
-            // all UMMAs and their commits (some arrive in other CTAs) have
-            // landed before the block leaves the cluster barrier below
+            // all UMMAs and their commits have landed before the block frees TMEM
             if (issued_any) {
                 umma_commit(fin);
                 drain_wait(fin, 0);
@@ -374,8 +357,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             Ring rg;
             uint32_t issued_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             int issued_mask = 0;
-            for (int g = cluster_id; g < P.num_groups && !*abort_flag; g += num_clusters) {
-                const int m_blk = (g / P.n_tiles) * P.cm + rank;
+            for (int g = blockIdx.x; g < P.num_units && !*abort_flag; g += gridDim.x) {
+                const int m_blk = g / P.n_tiles;
                 for (int part = 0; part < P.n_parts; ++part)
                 for (int jc = 0; jc < n_jc; ++jc) {
                     if (!mbar_wait(yempty0 + 8 * rg.stage, rg.phase ^ 1, abort_flag, kWaitLimitNs)) break;
@@ -402,13 +385,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         int lt = 0;
         float s0[kMaxCoilsPerTile], s1[kMaxCoilsPerTile];  // row sums, carried across a tile's sub-tiles
         for (int t = 0;; ++t, ++lt) {
-            const int g = cluster_id + (t / P.n_parts) * num_clusters, part = t % P.n_parts;
-            if (g >= P.num_groups) break;
+            const int g = (int)blockIdx.x + (t / P.n_parts) * (int)gridDim.x, part = t % P.n_parts;
+            if (g >= P.num_units) break;
             const int a = lt & 1;
             const uint32_t ap = (lt >> 1) & 1;
             if (!mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) break;
             fence_after_sync();
-            const int m_blk = (g / P.n_tiles) * P.cm + rank, n_blk = g % P.n_tiles;
+            const int m_blk = g / P.n_tiles, n_blk = g % P.n_tiles;
             if (part == 0) {
 #pragma unroll
                 for (int cs = 0; cs < kMaxCoilsPerTile; ++cs) s0[cs] = s1[cs] = 0.f;
@@ -479,7 +462,6 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         tmem_dealloc(tmem_base, P.tmem_cols);
     }
     if (threadIdx.x == 0 && *abort_flag) atomicExch(P.status, kStatusTimeout);
-    cluster_sync();  // no CTA leaves while a peer may still multicast into it or arrive on its barriers
 }
 
 // ---------------------------------------------------------------------------
@@ -514,18 +496,13 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
     uint32_t *tmem_slot = (uint32_t *)(bars + 2 * S + 2 * R + 5);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rank = (int)cluster_ctarank();
-    const int cluster_id = blockIdx.x / P.cm, num_clusters = gridDim.x / P.cm;
-    const uint32_t b_slice = b_bytes / (uint32_t)P.cm;  // rows ny_pad / cm
-    const uint16_t mask = cluster_mask(P.cm);
-    // unit u of group g: split p = u / m_tiles, tile m = u % m_tiles with the
-    // coil fastest (m = ib * nc + c); m_tiles is a multiple of cm, so all
-    // units of a group share the split and hence the B (conj A_y) rows
+    // unit u: split p = u / m_tiles, tile m = u % m_tiles with the coil
+    // fastest (m = ib * nc + c)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full0 + 8 * s, kAdjProducers + 1);  // producer threads + the B loads' expect_tx arrival
-            mbar_init(empty0 + 8 * s, P.cm);  // released by the UMMA commits of every CTA of the cluster
+            mbar_init(empty0 + 8 * s, 1);  // released by the UMMA commit
         }
         for (int r = 0; r < R; ++r) {
             mbar_init(rfull0 + 8 * r, 1);
@@ -551,7 +528,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         prefetch_tensormap(&t_y);
     }
     fence_before_sync();
-    cluster_sync();  // barriers of every CTA of the cluster are initialised before any multicast
+    __syncthreads();  // barriers initialised and TMEM allocated before any role starts
     fence_after_sync();
     const uint32_t tmem_base = *tmem_slot;
 
@@ -572,8 +549,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         Ring rr, rs;
         uint32_t issued_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int issued_mask = 0;
-        for (int g = cluster_id; g < P.num_groups && !*abort_flag; g += num_clusters) {
-            const int u = g * P.cm + rank;
+        for (int u = blockIdx.x; u < P.num_units && !*abort_flag; u += gridDim.x) {
             const int p = u / P.m_tiles;
             const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
             bool ok = true;
@@ -585,18 +561,12 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                 }
                 const uint32_t fb = full0 + 8 * rs.stage;
                 if (threadIdx.x == 0) {
-                    // this CTA's 1/cm of the conj(A_y) rows, delivered to the whole cluster
-                    const uint32_t sb = smem_u32(smem + (size_t)rs.stage * stage_bytes) + rank * b_slice;
-                    const int b_row = P.b_row0 + rank * (P.ny_pad / P.cm);
+                    // the stage's conj(A_y) rows, hi and lo
+                    const uint32_t sb = smem_u32(smem + (size_t)rs.stage * stage_bytes);
                     mbar_arrive_expect_tx(fb, 2u * b_bytes);
                     const int x0 = kb * kTcBlockK, x1 = x0 + (kTf32 ? kTcBlockK / 2 : 0);
-                    if (P.cm > 1) {
-                        tma_load_2d_multicast(sb, &tb_hi, fb, x0, b_row, mask);
-                        tma_load_2d_multicast(sb + b_bytes, &tb_lo, fb, x1, b_row, mask);
-                    } else {
-                        tma_load_2d(sb, &tb_hi, fb, x0, b_row);
-                        tma_load_2d(sb + b_bytes, &tb_lo, fb, x1, b_row);
-                    }
+                    tma_load_2d(sb, &tb_hi, fb, x0, P.b_row0);
+                    tma_load_2d(sb + b_bytes, &tb_lo, fb, x1, P.b_row0);
                     issued_phase[rs.stage] = rs.phase;
                     issued_mask |= 1 << rs.stage;
                 }
@@ -726,8 +696,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
             Ring rg;
             int lt = 0;
             bool issued_any = false;
-            for (int g = cluster_id; g < P.num_groups; g += num_clusters, ++lt) {
-                const int u = g * P.cm + rank;
+            for (int u = blockIdx.x; u < P.num_units; u += gridDim.x, ++lt) {
                 const int p = u / P.m_tiles;
                 const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
                 const int a = lt % NA;
@@ -764,18 +733,13 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                         }
                     }
                     issued_any = true;
-                    // the stage is free only when every CTA of the cluster has consumed it
-                    if (P.cm > 1)
-                        umma_commit_multicast(empty0 + 8 * rg.stage, mask);
-                    else
-                        umma_commit(empty0 + 8 * rg.stage);
+                    umma_commit(empty0 + 8 * rg.stage);  // the stage is free once these UMMAs completed
                     rg.next(S);
                 }
                 if (!ok) break;
                 umma_commit(tfull0 + 8 * a);
             }
-            // all UMMAs and their commits (some arrive in other CTAs) have
-            // landed before the block leaves the cluster barrier below
+            // all UMMAs and their commits have landed before the block frees TMEM
             if (issued_any) {
                 umma_commit(fin);
                 drain_wait(fin, 0);
@@ -787,8 +751,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
             Ring rg;
             uint32_t issued_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             int issued_mask = 0;
-            for (int g = cluster_id; g < P.num_groups && !*abort_flag; g += num_clusters) {
-                const int u = g * P.cm + rank;
+            for (int u = blockIdx.x; u < P.num_units && !*abort_flag; u += gridDim.x) {
                 const int p = u / P.m_tiles, m = u % P.m_tiles;
                 const int c = m % P.nc, ib = m / P.nc;
                 const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
@@ -823,8 +786,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         const int ii = kPx128 ? row : row >> 1, o = kPx128 ? 0 : row & 1;
         const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
         int lt = 0;
-        for (int g = cluster_id; g < P.num_groups; g += num_clusters, ++lt) {
-            const int u = g * P.cm + rank;
+        for (int u = blockIdx.x; u < P.num_units; u += gridDim.x, ++lt) {
             const int a = lt % NA;
             const uint32_t ap = (lt / NA) & 1;
             if (!mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) break;
@@ -878,7 +840,6 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         tmem_dealloc(tmem_base, P.tmem_cols);
     }
     if (threadIdx.x == 0 && *abort_flag) atomicExch(P.status, kStatusTimeout);
-    cluster_sync();  // no CTA leaves while a peer may still multicast into it or arrive on its barriers
 }
 
 // ---------------------------------------------------------------------------
@@ -941,10 +902,12 @@ uint32_t tmem_cols_for(int cols) {
 }
 
 // shared-memory plans: (operand stages, secondary ring stages, bytes)
+// The operand stages of either product: p->fwd_stages / p->adj_stages when
+// set (the autotuner's choice, 2..4), else as many as fit (at most 4).
 void fwd_smem_plan(const mri_plan *p, int *stages, int *ay_stages, size_t *bytes) {
     const int stage = 2 * kTileBytesA + 2 * p->fwd_block_n * 128;
     int r = 2;
-    int s = std::min(4, (kMaxSmem - kSmemSlack - r * kAyChunkBytes) / stage);
+    int s = std::min(p->fwd_stages > 0 ? p->fwd_stages : 4, (kMaxSmem - kSmemSlack - r * kAyChunkBytes) / stage);
     if (s >= 3 && kMaxSmem - kSmemSlack - s * stage >= 3 * kAyChunkBytes) r = 3;
     *stages = s;
     *ay_stages = r;
@@ -958,7 +921,7 @@ void adj_smem_plan(const mri_plan *p, int *stages, int *raw_stages, size_t *byte
     const int bn = p->adj_block_n;  // UMMA N: conj(A_y) operand rows per tile
     const int stage = 2 * bn * 128;
     const int raw = raw_bytes_for(p->adj_tile_px) + kRawYBytes;
-    int s = 4, r = 0, na = 2, col0 = 0;
+    int s = p->adj_stages > 0 ? p->adj_stages : 4, r = 0, na = 2, col0 = 0;
     for (; s >= 2; --s) {
         na = (round_up(2 * bn, 64) + 64 * s <= 512) ? 2 : 1;
         col0 = round_up(na * bn, 64);
@@ -984,7 +947,17 @@ decltype(&adj_tc_kernel<false, false>) adj_kernel_for(const mri_plan *p) {
     return w ? adj_tc_kernel<false, true> : adj_tc_kernel<false, false>;
 }
 
+void fwd_set_coils_per_tile(mri_plan *p, int cpt) {
+    p->fwd_coils_per_tile = cpt;
+    p->fwd_block_n = p->ny_pad > 256 ? 256 : cpt * p->ny_pad;
+    p->fwd_n_tiles = ceil_div(p->nc, cpt);
+}
+
 }  // namespace
+
+int tc_max_coils_per_tile(const mri_plan *p) {
+    return std::min(std::min(kMaxCoilsPerTile, p->nc), std::max(1, 256 / p->ny_pad));
+}
 
 bool tc_supported(const mri_plan *p, std::string *why) {
     int major = 0, minor = 0;
@@ -1008,11 +981,8 @@ bool tc_supported(const mri_plan *p, std::string *why) {
 int tc_plan_tiling(mri_plan *p) {
     // forward: whole coils per N tile, or one coil in sub-tiles of 256
     // columns when it is wider than one UMMA (ny_pad is then a multiple of 256)
-    const int cpt_max = std::min(kMaxCoilsPerTile, std::max(1, 256 / p->ny_pad));
-    const int n_tiles = ceil_div(p->nc, cpt_max);
-    p->fwd_coils_per_tile = ceil_div(p->nc, n_tiles);
-    p->fwd_block_n = p->ny_pad > 256 ? 256 : p->fwd_coils_per_tile * p->ny_pad;
-    p->fwd_n_tiles = ceil_div(p->nc, p->fwd_coils_per_tile);
+    const int n_tiles = ceil_div(p->nc, tc_max_coils_per_tile(p));
+    fwd_set_coils_per_tile(p, ceil_div(p->nc, n_tiles));
     p->fwd_m_tiles = ceil_div(2 * p->nk, kTcBlockM);
     // adjoint: 64 pixels as 128 embedded rows, or 128 pixels as 128 rows
     // with the complex structure in B (when the image is at most 128 columns
@@ -1087,91 +1057,74 @@ int tc_make_tensor_maps(mri_plan *p) {
         set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
         return MRI_ERR_CUDA;
     }
-    // default cluster sizes: 2 where the shape allows (multicast halves the
-    // shared-operand traffic and clusters of two pack the GPCs densely)
-    return tc_set_clusters(p, tc_cluster_valid_fwd(p, 2) ? 2 : 1, tc_cluster_valid_adj(p, 2) ? 2 : 1);
+    return tc_set_tiles(p, 0, 0, 0);
 }
 
 namespace {
 
-template <typename Kern, typename... Args>
-cudaError_t launch_clustered(Kern kernel, int grid, int block, size_t smem, int cm, cudaStream_t s, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cm;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
-
-// Clusters of size cm that can be resident at once (each CTA needs an SM).
+// Co-resident CTAs of a persistent kernel (one per SM with these shared-memory sizes).
 template <typename Kern>
-int resident_clusters(Kern kernel, int block, size_t smem, int cm, int num_sms) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cm * std::max(1, num_sms / cm));
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = smem;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cm;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess || n <= 0) {
+int resident_ctas(Kern kernel, int block, size_t smem, int num_sms) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess || per_sm <= 0) {
         cudaGetLastError();
-        n = num_sms / cm;
+        per_sm = 1;
     }
-    return std::max(1, std::min(n, num_sms / cm));
+    return std::max(1, per_sm) * num_sms;
 }
 
 }  // namespace
 
-bool tc_cluster_valid_fwd(const mri_plan *p, int cm) {
-    if (cm != 1 && cm != 2 && cm != 4 && cm != 8) return false;
-    return cm == 1 || (p->fwd_block_n % (8 * cm) == 0 && cm <= p->num_sms);
+bool tc_tiles_valid(const mri_plan *p, int cpt, int fwd_stages, int adj_stages) {
+    if (cpt < 1 || cpt > tc_max_coils_per_tile(p)) return false;
+    if (fwd_stages < 2 || fwd_stages > 4 || adj_stages < 2 || adj_stages > 4) return false;
+    mri_plan q = *p;  // shared-memory plans of the candidate configuration
+    fwd_set_coils_per_tile(&q, cpt);
+    q.fwd_stages = fwd_stages;
+    q.adj_stages = adj_stages;
+    int s, r;
+    size_t bytes;
+    fwd_smem_plan(&q, &s, &r, &bytes);
+    if (s != fwd_stages) return false;
+    adj_smem_plan(&q, &s, &r, &bytes);
+    return s == adj_stages && r >= 2;
 }
 
-bool tc_cluster_valid_adj(const mri_plan *p, int cm) {
-    if (cm != 1 && cm != 2 && cm != 4 && cm != 8) return false;
-    return cm == 1 || (p->adj_m_tiles % cm == 0 && p->adj_block_n % (8 * cm) == 0 && cm <= p->num_sms);
-}
-
-int tc_set_clusters(mri_plan *p, int fwd_cm, int adj_cm) {
-    if (fwd_cm == 0) fwd_cm = p->fwd_cluster;
-    if (adj_cm == 0) adj_cm = p->adj_cluster;
-    if (!tc_cluster_valid_fwd(p, fwd_cm) || !tc_cluster_valid_adj(p, adj_cm)) {
-        set_error("cluster size not valid for this shape");
+int tc_set_tiles(mri_plan *p, int cpt, int fwd_stages, int adj_stages) {
+    if (cpt == 0) cpt = p->fwd_coils_per_tile;
+    int s, r;
+    size_t bytes;
+    if (fwd_stages == 0 || adj_stages == 0) {  // keep the current (or the largest fitting) stage counts
+        mri_plan q = *p;
+        fwd_set_coils_per_tile(&q, cpt);
+        fwd_smem_plan(&q, &s, &r, &bytes);
+        if (fwd_stages == 0) fwd_stages = s;
+        adj_smem_plan(&q, &s, &r, &bytes);
+        if (adj_stages == 0) adj_stages = s;
+    }
+    if (!tc_tiles_valid(p, cpt, fwd_stages, adj_stages)) {
+        set_error("tile configuration not valid for this shape");
         return MRI_ERR_INVALID;
     }
-    // the shared B operand is fetched in cm row slices, one per CTA of the cluster
+    fwd_set_coils_per_tile(p, cpt);
+    p->fwd_stages = fwd_stages;
+    p->adj_stages = adj_stages;
     bool ok = make_operand_maps(p, &p->tm_bfwd_hi, &p->tm_bfwd_lo, p->bfwd_hi, p->bfwd_lo, p->bfwd_t, p->kx,
-                                (uint64_t)p->nc * p->ny_pad, p->fwd_block_n / fwd_cm) &&
+                                (uint64_t)p->nc * p->ny_pad, p->fwd_block_n) &&
               make_operand_maps(p, &p->tm_badj_hi, &p->tm_badj_lo, p->badj_hi, p->badj_lo, p->badj_t, p->kk,
-                                p->badj_rows, p->adj_block_n / adj_cm);
+                                p->badj_rows, p->adj_block_n);
     if (!ok) {
         set_error("cuTensorMapEncodeTiled failed");
         return MRI_ERR_CUDA;
     }
-    invalidate_graph(p);  // captured launches carry the old maps and cluster sizes
-    p->fwd_cluster = fwd_cm;
-    p->adj_cluster = adj_cm;
-    int s, r;
+    invalidate_graph(p);  // captured launches carry the old maps and tile shapes
     size_t fsm, asm_;
     fwd_smem_plan(p, &s, &r, &fsm);
     adj_smem_plan(p, &s, &r, &asm_);
     const bool t = p->precision == MRI_TF32;
-    p->fwd_grid = fwd_cm * (t ? resident_clusters(fwd_tc_kernel<true>, kFwdThreads, fsm, fwd_cm, p->num_sms)
-                              : resident_clusters(fwd_tc_kernel<false>, kFwdThreads, fsm, fwd_cm, p->num_sms));
-    p->adj_grid = adj_cm * resident_clusters(adj_kernel_for(p), kAdjThreads, asm_, adj_cm, p->num_sms);
+    p->fwd_grid = t ? resident_ctas(fwd_tc_kernel<true>, kFwdThreads, fsm, p->num_sms)
+                    : resident_ctas(fwd_tc_kernel<false>, kFwdThreads, fsm, p->num_sms);
+    p->adj_grid = resident_ctas(adj_kernel_for(p), kAdjThreads, asm_, p->num_sms);
     return MRI_OK;
 }
 
@@ -1198,20 +1151,22 @@ cudaError_t launch_fwd_tc(mri_plan *p, const float2 *image, const float2 *maps, 
     P.n_parts = p->ny_pad > 256 ? p->ny_pad / 256 : 1;
     P.pw = p->ny_pad > 256 ? 256 : p->ny_pad;
     P.num_kb = p->kx / kTcBlockK;
-    P.cm = p->fwd_cluster;
-    P.num_groups = ceil_div(p->fwd_m_tiles, P.cm) * p->fwd_n_tiles;
+    P.num_units = p->fwd_m_tiles * p->fwd_n_tiles;
     size_t smem;
     fwd_smem_plan(p, &P.stages, &P.ay_stages, &smem);
     P.tmem_cols = tmem_cols_for(2 * p->fwd_block_n);
     P.sc = p->scal;
     P.skip = skip;
     P.status = &p->scal->status;
-    const int grid = P.cm * std::min(P.num_groups, p->fwd_grid / P.cm);
+    const int grid = std::min(P.num_units, p->fwd_grid);
     timing_begin(p, s);
-    cudaError_t e = t ? launch_clustered(fwd_tc_kernel<true>, grid, kFwdThreads, smem, P.cm, s, p->tm_afwd_hi,
-                                         p->tm_afwd_lo, p->tm_bfwd_hi, p->tm_bfwd_lo, p->tm_ayT, P)
-                      : launch_clustered(fwd_tc_kernel<false>, grid, kFwdThreads, smem, P.cm, s, p->tm_afwd_hi,
-                                         p->tm_afwd_lo, p->tm_bfwd_hi, p->tm_bfwd_lo, p->tm_ayT, P);
+    if (t)
+        fwd_tc_kernel<true><<<grid, kFwdThreads, smem, s>>>(p->tm_afwd_hi, p->tm_afwd_lo, p->tm_bfwd_hi,
+                                                            p->tm_bfwd_lo, p->tm_ayT, P);
+    else
+        fwd_tc_kernel<false><<<grid, kFwdThreads, smem, s>>>(p->tm_afwd_hi, p->tm_afwd_lo, p->tm_bfwd_hi,
+                                                             p->tm_bfwd_lo, p->tm_ayT, P);
+    cudaError_t e = cudaGetLastError();
     timing_end(p, s);
     p->launches += 2;
     return e != cudaSuccess ? e : cudaGetLastError();
@@ -1229,15 +1184,14 @@ cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
     P.m_tiles = p->adj_m_tiles;
     P.kb_per_split = p->ksplit_blocks;
     P.num_kb = p->kk / kTcBlockK;
-    P.cm = p->adj_cluster;
-    P.num_groups = p->adj_m_tiles * p->ksplit / P.cm;
+    P.num_units = p->adj_m_tiles * p->ksplit;
     size_t smem;
     adj_smem_plan(p, &P.stages, &P.raw_stages, &smem, &P.n_acc, &P.a_col0);
     P.tmem_cols = tmem_cols_for(P.a_col0 + 64 * P.stages);
     P.sc = p->scal;
     P.skip = skip;
     P.status = &p->scal->status;
-    const int grid = P.cm * std::min(P.num_groups, p->adj_grid / P.cm);
+    const int grid = std::min(P.num_units, p->adj_grid);
     // one launch per 256-column part of the image (one launch when ny <= 256)
     const int n_parts = adj_parts(p);
     timing_begin(p, s);
@@ -1247,8 +1201,9 @@ cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
         P.part = p->part + (size_t)j0 * p->nx_pad;  // column j0 of every (split, coil) plane
         P.ny_lim = p->ny - j0;
         P.b_row0 = j0;
-        e = launch_clustered(adj_kernel_for(p), grid, kAdjThreads, smem, P.cm, s, p->tm_badj_hi, p->tm_badj_lo,
-                             p->tm_axT, p->adj_tile_px == 128 ? p->tm_axQ : p->tm_axT, p->tm_y, P);
+        adj_kernel_for(p)<<<grid, kAdjThreads, smem, s>>>(p->tm_badj_hi, p->tm_badj_lo, p->tm_axT,
+                                                          p->adj_tile_px == 128 ? p->tm_axQ : p->tm_axT, p->tm_y, P);
+        e = cudaGetLastError();
         p->launches += 1;
     }
     timing_end(p, s);

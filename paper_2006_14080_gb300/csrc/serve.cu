@@ -8,8 +8,9 @@
 // start as slots and memory free up and their kernels overlap on the GPU.
 // DFT factors are kept resident in a plan cache keyed by shape and trajectory
 // (idle plans are evicted least-recently-used when the budget needs room);
-// per-request buffers come from a stream-ordered pool, so no step of the loop
-// but the eviction of a cached plan synchronises the device.  Each request is reconstructed by exactly
+// plans and per-request buffers come from a stream-ordered pool and are
+// freed stream-ordered, so no step of the loop, eviction included,
+// synchronises the device.  Each request is reconstructed by exactly
 // the kernels it would use alone (own plan, own workspace), so its result
 // does not depend on what else is in flight.
 #include <algorithm>

@@ -1,8 +1,9 @@
-// Persistent autotuning results: the cluster sizes that mri_plan_autotune
-// chose, keyed by precision, problem shape and SM count, kept in a
+// Persistent autotuning results: the tile configuration that
+// mri_plan_autotune chose (coils per forward N tile, forward and adjoint
+// operand stages), keyed by precision, problem shape and SM count, kept in a
 // process-wide table that plans consult when they are created, and saved to
-// or loaded from a small JSON file.  The cluster sizes change the schedule of
-// the tensor-core products only, never their arithmetic, so a stale or
+// or loaded from a small JSON file.  The configuration changes the schedule
+// of the tensor-core products only, never their arithmetic, so a stale or
 // foreign table can cost speed but never change a result.
 #include <cctype>
 #include <cstdio>
@@ -21,7 +22,8 @@ namespace {
 using Key = std::tuple<int, int, int, int, int, int>;  // precision, nx, ny, nk, nc, sms
 
 std::mutex g_mu;
-std::map<Key, std::pair<int, int>> g_table;  // -> (forward cluster, adjoint cluster)
+using Tiles = std::tuple<int, int, int>;  // forward coils per tile, forward stages, adjoint stages
+std::map<Key, Tiles> g_table;
 
 Key key_of(const mri_plan *p) { return Key(p->precision, p->nx, p->ny, p->nk, p->nc, p->num_sms); }
 
@@ -46,15 +48,16 @@ bool find_int(const std::string &s, size_t b, size_t e, const char *name, long l
 
 void tuning_record(const mri_plan *p) {
     std::lock_guard<std::mutex> lock(g_mu);
-    g_table[key_of(p)] = {p->fwd_cluster, p->adj_cluster};
+    g_table[key_of(p)] = Tiles(p->fwd_coils_per_tile, p->fwd_stages, p->adj_stages);
 }
 
-bool tuning_lookup(const mri_plan *p, int *fwd_cluster, int *adj_cluster) {
+bool tuning_lookup(const mri_plan *p, int *fwd_coils_per_tile, int *fwd_stages, int *adj_stages) {
     std::lock_guard<std::mutex> lock(g_mu);
     auto it = g_table.find(key_of(p));
     if (it == g_table.end()) return false;
-    *fwd_cluster = it->second.first;
-    *adj_cluster = it->second.second;
+    *fwd_coils_per_tile = std::get<0>(it->second);
+    *fwd_stages = std::get<1>(it->second);
+    *adj_stages = std::get<2>(it->second);
     return true;
 }
 
@@ -71,13 +74,13 @@ MRI_API int mri_tuning_save(const char *path) {
         std::lock_guard<std::mutex> lock(g_mu);
         bool first = true;
         for (const auto &kv : g_table) {
-            char buf[256];
+            char buf[320];
             std::snprintf(buf, sizeof(buf),
                           "%s\n  {\"precision\": %d, \"nx\": %d, \"ny\": %d, \"nk\": %d, \"nc\": %d, \"sms\": %d, "
-                          "\"fwd_cluster\": %d, \"adj_cluster\": %d}",
+                          "\"fwd_coils_per_tile\": %d, \"fwd_stages\": %d, \"adj_stages\": %d}",
                           first ? "" : ",", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
-                          std::get<3>(kv.first), std::get<4>(kv.first), std::get<5>(kv.first), kv.second.first,
-                          kv.second.second);
+                          std::get<3>(kv.first), std::get<4>(kv.first), std::get<5>(kv.first),
+                          std::get<0>(kv.second), std::get<1>(kv.second), std::get<2>(kv.second));
             text += buf;
             first = false;
         }
@@ -103,20 +106,24 @@ MRI_API int mri_tuning_load(const char *path) {
         return set_error(std::string(path) + " is not a tuning file"), MRI_ERR_INVALID;
     const size_t list = s.find("\"entries\"");
     if (list == std::string::npos) return set_error("tuning file has no entries"), MRI_ERR_INVALID;
-    std::map<Key, std::pair<int, int>> parsed;
+    std::map<Key, Tiles> parsed;
     size_t b = s.find('{', list);
     while (b != std::string::npos) {
         const size_t e = s.find('}', b);
         if (e == std::string::npos) return set_error("unterminated tuning entry"), MRI_ERR_INVALID;
-        const char *names[] = {"precision", "nx", "ny", "nk", "nc", "sms", "fwd_cluster", "adj_cluster"};
-        long long v[8];
-        for (int q = 0; q < 8; ++q)
+        const char *names[] = {"precision", "nx",         "ny",         "nk",        "nc",
+                               "sms",       "fwd_coils_per_tile", "fwd_stages", "adj_stages"};
+        long long v[9];
+        for (int q = 0; q < 9; ++q)
             if (!find_int(s, b, e, names[q], &v[q]))
                 return set_error(std::string("tuning entry without integer \"") + names[q] + "\""), MRI_ERR_INVALID;
-        for (int q = 6; q < 8; ++q)
-            if (v[q] != 1 && v[q] != 2 && v[q] != 4 && v[q] != 8)
-                return set_error("tuning entry with a cluster size other than 1, 2, 4, 8"), MRI_ERR_INVALID;
-        parsed[Key((int)v[0], (int)v[1], (int)v[2], (int)v[3], (int)v[4], (int)v[5])] = {(int)v[6], (int)v[7]};
+        if (v[6] < 1 || v[6] > 4)
+            return set_error("tuning entry with coils per tile outside 1..4"), MRI_ERR_INVALID;
+        for (int q = 7; q < 9; ++q)
+            if (v[q] < 2 || v[q] > 4)
+                return set_error("tuning entry with a stage count outside 2..4"), MRI_ERR_INVALID;
+        parsed[Key((int)v[0], (int)v[1], (int)v[2], (int)v[3], (int)v[4], (int)v[5])] =
+            Tiles((int)v[6], (int)v[7], (int)v[8]);
         b = s.find('{', e);
     }
     std::lock_guard<std::mutex> lock(g_mu);

@@ -63,9 +63,9 @@ def test_tuning_table_round_trip(lib, tmp_path):
     src = tmp_path / "tuned.json"
     src.write_text('{"format": "mrirecon-tuning", "version": 1, "entries": [\n'
                    ' {"precision": 2, "nx": 128, "ny": 128, "nk": 16384, "nc": 12, "sms": 152,'
-                   ' "fwd_cluster": 4, "adj_cluster": 1},\n'
+                   ' "fwd_coils_per_tile": 2, "fwd_stages": 3, "adj_stages": 3},\n'
                    ' {"precision": 1, "nx": 256, "ny": 256, "nk": 65536, "nc": 32, "sms": 152,'
-                   ' "fwd_cluster": 1, "adj_cluster": 2}\n]}\n')
+                   ' "fwd_coils_per_tile": 1, "fwd_stages": 2, "adj_stages": 2}\n]}\n')
     mr.tuning_clear()
     assert mr.tuning_count() == 0
     mr.tuning_load(str(src))
@@ -82,7 +82,9 @@ def test_tuning_table_round_trip(lib, tmp_path):
     bad = [('{"format": "other"}', "not a tuning file"),
            ('{"format": "mrirecon-tuning", "entries": [{"precision": 2, "nx": 8}]}', "without integer"),
            ('{"format": "mrirecon-tuning", "entries": [{"precision": 2, "nx": 8, "ny": 8, "nk": 8, "nc": 1,'
-            ' "sms": 152, "fwd_cluster": 3, "adj_cluster": 1}]}', "cluster size")]
+            ' "sms": 152, "fwd_coils_per_tile": 5, "fwd_stages": 3, "adj_stages": 3}]}', "coils per tile"),
+           ('{"format": "mrirecon-tuning", "entries": [{"precision": 2, "nx": 8, "ny": 8, "nk": 8, "nc": 1,'
+            ' "sms": 152, "fwd_coils_per_tile": 1, "fwd_stages": 5, "adj_stages": 3}]}', "stage count")]
     for text, why in bad:
         f = tmp_path / "bad.json"
         f.write_text(text)

@@ -1,16 +1,21 @@
 """Parity at the full N=256 size (32 coils, 128 golden-angle spokes x 512
 samples, nk = 65536) in the launch configuration the benchmark times
-(autotuned cluster sizes, graph replay on a created stream).
+(autotuned tile configuration, graph replay on a created stream).
 
 The FP64 oracle computes the full forward operator of the phantom at this
 size (about 1.1 TFLOP, tens of seconds on the host), compared entry by entry;
 the adjoint and the normal operator are checked at sampled pixels (the oracle
 evaluates single pixels directly), and the first ADMM iterate (one outer
 step with one CG step, whose global scalars need one full adjoint and one
-full normal operator in the oracle) in full.  The whole 50 x 10
-reconstruction is then checked by properties that hold at any size: a finite
-image, a non-increasing objective, and agreement of the TF32 and BF16x3 forms.
+full normal operator in the oracle) in full.  A reconstruction at a reduced
+count of 3 ADMM x 3 CG steps (12 normal operators, stored by
+tests/golden/make_golden.py from the oracle) is compared image for image.
+The whole 50 x 10 reconstruction is then checked by properties that hold at
+any size: a finite image, a non-increasing objective, and agreement of the
+TF32 and BF16x3 forms.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -100,6 +105,31 @@ def test_full_size_first_admm_iterate(mr, case, plan, first_iterate):
         got = mr.admm_reconstruct(pl, _dev(d), _dev(p.maps), p.lam, p.beta, 1, 1).cpu().numpy()
         pl.sync_status()
     assert _rel(got, x1) <= 2 * OP_TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp32"])
+def test_full_size_reconstruction_3x3_matches_oracle(mr, case, precision):
+    p, x, y, pix, fx, d = case
+    path = os.path.join(os.path.dirname(__file__), "golden", "admm_n256_c32_s128x512_admm3x3.npz")
+    g = np.load(path)
+    # the measurement regenerated here is the one the stored run used
+    assert abs(np.linalg.norm(d.astype(np.complex128)) - float(g["d_norm"])) <= 1e-9 * float(g["d_norm"])
+    assert np.array_equal(d.reshape(-1)[g["d_idx"]], g["d_samples"])
+    assert (int(g["admm_iters"]), int(g["cg_iters"])) == (3, 3)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        with mr.Plan(p.nx, p.ny, p.nc, _dev(p.traj, torch.float32), precision) as pl:
+            if precision != "fp32":
+                pl.autotune(repeats=2)
+            obj = torch.zeros(3, dtype=torch.float64, device="cuda")
+            img = mr.admm_reconstruct(pl, _dev(d), _dev(p.maps), p.lam, p.beta, 3, 3,
+                                      objective_hist=obj).cpu().numpy()
+            o = obj.cpu().numpy()
+            pl.sync_status()
+    err = _rel(img, g["x"])
+    print(f"N=256 3x3 {precision}: NRMSE vs FP64 oracle = {err:.3e}")
+    assert err <= 1e-3
+    assert np.allclose(o, g["objective"], rtol=1e-3, atol=0)
 
 
 def test_full_size_reconstruction_properties(mr, case):

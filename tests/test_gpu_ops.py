@@ -150,29 +150,33 @@ def test_degenerate_shapes(mr, precision):
         assert _rel(adj, oracle.adjoint(traj, y, maps)) <= OP_TOL[precision]
 
 
-def test_cluster_sizes_change_schedule_not_results(mr):
-    # the B operand is multicast within clusters of 1..8 CTAs; every cluster
-    # size must give bit-identical products (same arithmetic, same order)
+def test_tile_configurations_change_schedule_not_results(mr):
+    # coils per forward tile and the stage counts of both operand rings change
+    # the schedule only; every valid configuration must give bit-identical
+    # products (same arithmetic, same order)
     nx, ny, nc = 128, 128, 12
     maps, traj, x, y = _case(nx, ny, nc, 24, 256, seed=31)
     with mr.Plan(nx, ny, nc, _dev(traj, torch.float32), "bf16x3") as plan:
         dm, dx, dy = _dev(maps), _dev(x), _dev(y)
         ref_f = ref_a = None
-        tried = 0
-        for cm in (1, 2, 4, 8):
-            try:
-                plan.set_clusters(cm, cm)
-            except mr.MriError:
-                continue
-            tried += 1
-            f = mr.nudft_forward(plan, dx, dm).cpu().numpy()
-            a = mr.nudft_adjoint(plan, dy, dm).cpu().numpy()
-            if ref_f is None:
-                ref_f, ref_a = f, a
-            assert np.array_equal(f, ref_f) and np.array_equal(a, ref_a), cm
-        assert tried >= 2
+        tried = set()
+        for cpt in (1, 2, 3, 4):
+            for fs, ast in ((2, 2), (3, 3), (4, 4), (2, 4)):
+                try:
+                    plan.set_tiles(cpt, fs, ast)
+                except mr.MriError:
+                    continue
+                tried.add((cpt, fs, ast))
+                f = mr.nudft_forward(plan, dx, dm).cpu().numpy()
+                a = mr.nudft_adjoint(plan, dy, dm).cpu().numpy()
+                if ref_f is None:
+                    ref_f, ref_a = f, a
+                assert np.array_equal(f, ref_f) and np.array_equal(a, ref_a), (cpt, fs, ast)
+        assert len({t[0] for t in tried}) >= 2 and len(tried) >= 4
+        with pytest.raises(mr.MriError):
+            plan.set_tiles(5, 2, 2)
         cfg = plan.autotune(repeats=2)
-        assert cfg["fwd_cluster"] in (1, 2, 4, 8) and cfg["adj_cluster"] in (1, 2, 4, 8)
+        assert (cfg["fwd_coils_per_tile"], cfg["fwd_stages"], cfg["adj_stages"]) in tried
         assert np.array_equal(mr.nudft_forward(plan, dx, dm).cpu().numpy(), ref_f)
         plan.sync_status()
     assert _rel(ref_f, oracle.forward(traj, x, maps)) <= OP_TOL["bf16x3"]
@@ -198,8 +202,8 @@ def test_invalid_arguments_are_rejected(mr):
 
 
 def test_tuning_table_sets_new_plans(mr, tmp_path):
-    # a plan created for a shape the tuning table holds starts with its cluster
-    # sizes; autotune records its choice for the next plan of the same shape
+    # a plan created for a shape the tuning table holds starts with its tile
+    # configuration; autotune records its choice for the next plan of the same shape
     nx, ny, nc = 128, 128, 12
     maps, traj, x, y = _case(nx, ny, nc, 24, 256, seed=41)
     t = _dev(traj, torch.float32)
@@ -207,14 +211,14 @@ def test_tuning_table_sets_new_plans(mr, tmp_path):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     f = tmp_path / "t.json"
     f.write_text('{"format": "mrirecon-tuning", "version": 1, "entries": [{"precision": 2, "nx": %d, "ny": %d, '
-                 '"nk": %d, "nc": %d, "sms": %d, "fwd_cluster": 1, "adj_cluster": 4}]}' % (nx, ny, nk, nc, sms))
+                 '"nk": %d, "nc": %d, "sms": %d, "fwd_coils_per_tile": 1, "fwd_stages": 3, "adj_stages": 2}]}'
+                 % (nx, ny, nk, nc, sms))
     mr.tuning_clear()
     mr.tuning_load(str(f))
     with mr.Plan(nx, ny, nc, t, "bf16x3") as plan:
         cfg = plan.config()
-        assert (cfg["fwd_cluster"], cfg["adj_cluster"]) == (1, 4)
+        assert (cfg["fwd_coils_per_tile"], cfg["fwd_stages"], cfg["adj_stages"]) == (1, 3, 2)
         tuned = plan.autotune(repeats=2)
     with mr.Plan(nx, ny, nc, t, "bf16x3") as plan:
-        cfg = plan.config()
-        assert (cfg["fwd_cluster"], cfg["adj_cluster"]) == (tuned["fwd_cluster"], tuned["adj_cluster"])
+        assert plan.config() == tuned
     mr.tuning_clear()
