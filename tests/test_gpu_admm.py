@@ -63,25 +63,34 @@ def _nrmse(x, ref):
     return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
 
 
+# Per-iterate bars of the N=32 workload.  The final image is held to the
+# 1e-3 target for both forms.  The intermediate iterates are more sensitive
+# than the final one: with 5 CG steps per x-update the second ADMM step
+# amplifies the operator error of the first by about 300 in an emulation of
+# the BF16x3 products (1.8e-5 NRMSE after step 1, 5.9e-3 after step 2, 5e-4
+# after step 10), and by about 70 for FP32 vectors with exact operators.
+# So the objective and the relative change of every step are held tightly
+# for the FP32 form (emulation: 1.1e-4 and 2.3e-3 at most) and, for BF16x3,
+# at the first step (operator error only) and the last.
+HIST_TOL = {"fp32": {"obj": 1e-3, "alpha": 2e-2}, "bf16x3": {"obj": 1e-1, "alpha": 0.5}}
+
+
 @pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 def test_admm_small_matches_oracle(mr, precision):
-    # The N=32 workload is far more sensitive to per-application operator
-    # error than the N=128 one: the FP64 oracle itself moves by ~3e-3 NRMSE
-    # when every normal-operator application carries 1e-6 relative noise (the
-    # size of FP32 operator error).  Its bar is therefore the paper's own
-    # FP32-versus-FP64 difference for ADMM, about 1% (Section V); the 1e-3
-    # target is held on the N=128 workload below.
     p = synth.config_small()
     g, d = _golden(p)
     x, obj, alp = _run(mr, p, d, precision)
     err = _nrmse(x, g["x"])
     print(f"small workload {precision}: NRMSE vs FP64 oracle = {err:.3e}")
-    assert err <= 1e-2
-    # the objective decreases monotonically and ends where the oracle's does
-    assert np.all(np.diff(obj) <= 1e-6 * np.abs(obj[:-1]))
+    assert err <= NRMSE_TOL
+    # histories follow the oracle's: every step within the form's bar, the
+    # first (before any amplification) and the last within 1e-4 and 1e-3
+    assert np.allclose(obj, g["objective"], rtol=HIST_TOL[precision]["obj"], atol=0)
     assert abs(obj[0] / g["objective"][0] - 1) <= 1e-4
-    assert abs(obj[-1] / g["objective"][-1] - 1) <= 1e-2
-    assert np.all(alp > 0) and alp[0] == 1.0
+    assert abs(obj[-1] / g["objective"][-1] - 1) <= NRMSE_TOL
+    assert np.all(np.diff(obj) <= 1e-6 * np.abs(obj[:-1]))
+    assert alp[0] == 1.0 and g["alpha"][0] == 1.0
+    assert np.allclose(alp[1:], g["alpha"][1:], rtol=HIST_TOL[precision]["alpha"], atol=0)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
@@ -96,9 +105,9 @@ def test_admm_medium_matches_oracle(mr, precision):
 
 def test_admm_medium_tf32_reported(mr):
     # The TF32 form carries ~4e-4 relative error per operator application
-    # (10-bit operand mantissas), forty times the BF16x3 form's, so it is not
-    # held to the 1e-3 image bar; it is held to the paper's ~1% FP32-vs-FP64
-    # level and its measured NRMSE is printed.
+    # (10-bit operand mantissas), forty times the BF16x3 form's: it fails the
+    # 1e-5 operator and 1e-3 image targets, is reported as failing them, and
+    # is held here only to the paper's ~1% FP32-vs-FP64 level.
     p = synth.config_medium()
     g, d = _golden(p)
     x, _, _ = _run(mr, p, d, "tf32", with_hist=False)
@@ -121,7 +130,14 @@ def test_admm_table1_tolerances_stop_like_oracle(mr, precision):
     steps = int(np.sum(alp >= 0))
     assert 1 <= steps <= t1["admm_max_iterations"]
     assert steps == ref["steps"]
-    assert _nrmse(x, ref["x"]) <= 1e-2
+    # Table I's lambda = 1e-7 leaves the problem barely regularised and 20 CG
+    # steps deep: FP32 vector storage alone moves the FP64 solver by 1.3e-3
+    # and a reordering of its FP64 sums by 4.7e-4
+    # (test_table1_small_workload_amplifies_any_rounding), so the bar is the
+    # paper's ~1% FP32-vs-FP64 difference (Section V)
+    err = _nrmse(x, ref["x"])
+    print(f"small workload, Table I parameters, {precision}: NRMSE vs FP64 oracle = {err:.3e}")
+    assert err <= 1e-2
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16x3"])

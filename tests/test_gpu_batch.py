@@ -69,10 +69,13 @@ def test_batch_equals_alone(mr, precision):
     for a, b, c in zip(first, second, alone):
         assert np.all(np.isfinite(a))
         assert np.array_equal(a, b) and np.array_equal(a, c)
-    # the N=32 member against the FP64 oracle (bar as in test_gpu_admm)
+    # the N=32 member against the FP64 oracle: the 1e-3 image bar of
+    # test_gpu_admm for FP32 and BF16x3; TF32 (10-bit operand mantissas,
+    # ~4e-4 operator error) does not meet it and is held to 5%, the typical
+    # error of a compressed-sensing reconstruction itself (Section V)
     g = oracle.admm(probs[0].traj, probs[0].maps, oracle.measurements(probs[0]), probs[0].lam, probs[0].beta,
                     probs[0].admm_iters, probs[0].cg_iters)["x"]
-    assert np.linalg.norm(first[0] - g) / np.linalg.norm(g) <= (5e-2 if precision == "tf32" else 1e-2)  # TF32: the paper's 5% (Section V)
+    assert np.linalg.norm(first[0] - g) / np.linalg.norm(g) <= (5e-2 if precision == "tf32" else 1e-3)
 
 
 def test_batch_rejects_shared_plans(mr):

@@ -87,7 +87,9 @@ def test_serve_mix_equals_alone(mr, precision):
         assert np.array_equal(_direct(mr, probs[q], data[q], precision), alone[q])
     g = oracle.admm(probs[0].traj, probs[0].maps, data[0], probs[0].lam, probs[0].beta, probs[0].admm_iters,
                     probs[0].cg_iters)["x"]
-    assert np.linalg.norm(alone[0] - g) / np.linalg.norm(g) <= (5e-2 if precision == "tf32" else 1e-2)  # TF32: the paper's 5% (Section V)
+    # the N=32 request against the FP64 oracle: 1e-3 for FP32 and BF16x3 as in
+    # test_gpu_admm; TF32 misses that bar and is held to 5% (Section V)
+    assert np.linalg.norm(alone[0] - g) / np.linalg.norm(g) <= (5e-2 if precision == "tf32" else 1e-3)
 
 
 def test_serve_budget_admission(mr):
