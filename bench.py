@@ -214,6 +214,45 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def with_cpu_leg(args, rank, world) -> bool:
+    """The CPU-baseline leg (the FP64 oracle on the host) runs on rank 0 of a
+    one-GPU run only."""
+    return not args.no_cpu_baseline and world == 1 and rank == 0
+
+
+def oracle_measurement(p):
+    """CPU-baseline leg: the problem's measurement formed with the FP64 oracle's
+    forward operator plus the seeded noise (how the stored oracle
+    reconstructions under tests/golden were made)."""
+    import oracle
+    return oracle.measurements(p)
+
+
+def kspace_is_oracle(kspace_np, gpath) -> bool:
+    """Whether kspace_np is the input of the stored oracle reconstruction
+    (its L2 norm and sampled entries match the stored fingerprint)."""
+    g = np.load(gpath)
+    flat = np.asarray(kspace_np).reshape(-1)
+    norm = float(np.linalg.norm(flat.astype(np.complex128)))
+    return abs(norm - float(g["d_norm"])) <= 1e-9 * float(g["d_norm"]) and \
+        np.array_equal(flat[g["d_idx"]], g["d_samples"])
+
+
+def clock_scaled_peak(pk, clocks):
+    """Dense BF16 peak for the product kernels: the measured burst figure when
+    they ran at the maximum SM clock (median within 3% of it), else the
+    measured sustained figure (a kernel held below the maximum clock by the
+    power cap through a long step, as the sustained cuBLAS loop was)."""
+    burst = float(pk["bf16_tflops"])
+    sustained = float(pk.get("bf16_tflops_sustained", burst))
+    sm, smax = clocks.get("sm_mhz"), clocks.get("sm_max_mhz")
+    if not sm or not smax:
+        return burst, "burst bf16 (no clock samples)"
+    if float(sm) >= 0.97 * float(smax):
+        return burst, f"burst bf16 (median SM clock {sm:.0f} of {smax:.0f} MHz)"
+    return sustained, f"sustained bf16 (median SM clock {sm:.0f} of {smax:.0f} MHz, below the maximum)"
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_2006_14080_gb300 as mr
@@ -234,10 +273,20 @@ def run_gpu(args, rank, world, local_rank):
     maps = torch.from_numpy(p.maps).to(dev)
     ximg = torch.from_numpy(p.image_true).to(dev)
 
-    # measurement: the library's FP32 forward model of the phantom plus the seeded noise
-    with mr.Plan(p.nx, p.ny, p.nc, traj, "fp32") as plan32:
-        d_clean = mr.nudft_forward(plan32, ximg, maps).cpu().numpy()
-    kspace_np = synth.add_noise(d_clean, p.noise, p.noise_level)
+    # measurement: the phantom's k-space plus the seeded noise.  On rank 0 of a
+    # one-GPU run the CPU-baseline leg forms it with the FP64 oracle's forward
+    # operator, exactly as the stored oracle reconstructions were made, so that
+    # the reported NRMSE compares images of the same input; otherwise with the
+    # library's FP32 forward operator.
+    kspace_np, measurement = None, "library FP32 forward operator + seeded noise"
+    if with_cpu_leg(args, rank, world) and os.path.exists(os.path.join(ROOT, "tests", "golden",
+                                                                        f"admm_{p.name}.npz")):
+        kspace_np = oracle_measurement(p)
+        measurement = "FP64 oracle forward operator + seeded noise (the stored oracle reconstruction's input)"
+    if kspace_np is None:
+        with mr.Plan(p.nx, p.ny, p.nc, traj, "fp32") as plan32:
+            d_clean = mr.nudft_forward(plan32, ximg, maps).cpu().numpy()
+        kspace_np = synth.add_noise(d_clean, p.noise, p.noise_level)
     kspace = torch.from_numpy(kspace_np).to(dev)
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -364,7 +413,7 @@ def run_gpu(args, rank, world, local_rank):
     dom_avg_ms = adj_avg if dom == "adj" else fwd_avg
     executed = 3.0 * flops_prod  # hi*hi + hi*lo + lo*hi bf16 tensor products
     achieved = executed / (dom_avg_ms * 1e-3) / 1e12
-    peak_tf = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    peak_tf, peak_note = clock_scaled_peak(pk, clocks)
     # with tolerance exits the operator count is data-dependent: count the
     # ADMM steps one reconstruction takes and leave the TFLOP/s out
     tol_steps = None
@@ -381,7 +430,7 @@ def run_gpu(args, rank, world, local_rank):
     traffic, traffic_src = captured_traffic(dom_kernel, p.name)
     nrmse_vs_golden = None
     gpath = os.path.join(ROOT, "tests", "golden", f"admm_{p.name}.npz")
-    if os.path.exists(gpath):
+    if os.path.exists(gpath) and kspace_is_oracle(kspace_np, gpath):
         xg = np.load(gpath)["x"]
         nrmse_vs_golden = {"bf16x3": float(np.linalg.norm(x_bf16 - xg) / np.linalg.norm(xg))}
         if x_fp32 is not None:
@@ -413,8 +462,8 @@ def run_gpu(args, rank, world, local_rank):
                      "traffic": traffic, "traffic_unit": "bytes per launch", "traffic_source": traffic_src,
                      "note": f"executed bf16 tensor flops (3 products x 8*nk*nx*ny*nc) per launch / mean launch "
                              f"time ({dom_avg_ms:.4f} ms over {timing[dom + '_launches']} launches, CUDA events on "
-                             f"the launching stream in a directly-launched pass of the same steps), "
-                             f"peak = {pk_kind} sustained bf16"},
+                             f"the launching stream in a directly-launched pass of the same steps); peak = "
+                             f"{pk_kind} {peak_note}"},
         "nudft": {"fwd_ms_per_launch": fwd_avg, "adj_ms_per_launch": adj_avg,
                   "fwd_useful_tflops": flops_prod / (fwd_avg * 1e-3) / 1e12,
                   "adj_useful_tflops": flops_prod / (adj_avg * 1e-3) / 1e12,
@@ -430,6 +479,7 @@ def run_gpu(args, rank, world, local_rank):
         "gemm_peaks_tflops": gemm_peaks,
         "tf32_form": None,
         "nrmse_vs_fp64_oracle": nrmse_vs_golden,
+        "measurement": measurement,
         "tolerances": None if tol_steps is None else {"rtol": p.rtol, "atol": p.atol, "admm_steps_taken": tol_steps,
                                                       "admm_iters_max": p.admm_iters, "cg_iters_max": p.cg_iters},
         "paper_context_s": PAPER_TIMES_S.get(p.name),
@@ -471,9 +521,133 @@ def run_gpu(args, rank, world, local_rank):
         line["fp32_form"] = None
     if "e2e" not in forms:
         line["e2e"] = None
-    if not args.no_cpu_baseline and world == 1:
+    if args.extras and world == 1 and args.workload == "n128":
+        # the other single-GPU workloads, each as a sub-object of this line
+        line["small"] = small_block(args, mr, dev, with_cpu_leg(args, rank, world))
+        line["large"] = large_block(args, mr, dev, pk, pk_kind)
+        line["serve"] = serve_block(args, mr, dev)
+    if with_cpu_leg(args, rank, world):
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
     return line
+
+
+def _graph_rate(mr, plan, p, kspace, maps, out, steps, warmup, flush, stream, traj=None):
+    """recon/s of one plan with graph replay: warm-up, then `steps` timed
+    reconstructions (CUDA events on the launching stream, L2 flushed before
+    each).  Returns (recon/s, ms per step, launches per step)."""
+    import torch
+    def one():
+        if traj is not None:
+            plan.set_trajectory(traj)
+        mr.admm_reconstruct(plan, kspace, maps, p.lam, p.beta, p.admm_iters, p.cg_iters, out=out)
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    l0 = plan.launch_count()
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(stream)
+        one()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    return 1e3 / ms, ms, (plan.launch_count() - l0) // steps
+
+
+def small_block(args, mr, dev, oracle_input):
+    """The N=32 workload (4 coils, 16 uniform spokes x 64, 10 ADMM x 5 CG) in
+    the FP32 and BF16x3 forms: recon/s and NRMSE against the stored FP64
+    oracle reconstruction of the same input."""
+    import torch
+    p = synth.config_small()
+    stream = torch.cuda.current_stream()
+    traj, maps = torch.from_numpy(p.traj).to(dev), torch.from_numpy(p.maps).to(dev)
+    if oracle_input:
+        kspace_np = oracle_measurement(p)
+    else:
+        with mr.Plan(p.nx, p.ny, p.nc, traj, "fp32") as p32:
+            kspace_np = synth.add_noise(mr.nudft_forward(p32, torch.from_numpy(p.image_true).to(dev),
+                                                         maps).cpu().numpy(), p.noise, p.noise_level)
+    kspace = torch.from_numpy(kspace_np).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = torch.empty((p.nx, p.ny), dtype=torch.complex64, device=dev)
+    gpath = os.path.join(ROOT, "tests", "golden", f"admm_{p.name}.npz")
+    same = os.path.exists(gpath) and kspace_is_oracle(kspace_np, gpath)
+    res = {"workload": workload_name(p), "steps": args.steps, "warmup": args.warmup}
+    for prec in ("fp32", "bf16x3"):
+        with mr.Plan(p.nx, p.ny, p.nc, traj, prec) as plan:
+            rate, ms, launches = _graph_rate(mr, plan, p, kspace, maps, out, args.steps, args.warmup, flush, stream)
+            x = out.cpu().numpy()
+        entry = {"value": rate, "unit": "recon/s", "ms_per_step": ms, "gpu_launches_per_step": launches}
+        if same:
+            xg = np.load(gpath)["x"]
+            entry["nrmse_vs_fp64_oracle"] = float(np.linalg.norm(x - xg) / np.linalg.norm(xg))
+        res[prec] = entry
+    return res
+
+
+def large_block(args, mr, dev, pk, pk_kind):
+    """The N=256 workload (32 coils, 128 golden-angle spokes x 512, 50 ADMM x
+    10 CG) in the BF16x3 form: recon/s with graph replay (1 warm-up, 2 timed
+    steps, L2 flushed), and the roofline of its dominant product kernel from
+    one directly-launched, event-timed reconstruction.  Input: the library's
+    FP32 forward operator plus the seeded noise (image parity at this size is
+    a GPU test against the oracle's 3 x 3 reconstruction)."""
+    import torch
+    p = synth.config_large()
+    stream = torch.cuda.current_stream()
+    traj, maps = torch.from_numpy(p.traj).to(dev), torch.from_numpy(p.maps).to(dev)
+    with mr.Plan(p.nx, p.ny, p.nc, traj, "fp32") as p32:
+        d = mr.nudft_forward(p32, torch.from_numpy(p.image_true).to(dev), maps).cpu().numpy()
+    kspace = torch.from_numpy(synth.add_noise(d, p.noise, p.noise_level)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = torch.empty((p.nx, p.ny), dtype=torch.complex64, device=dev)
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or 0)
+    with mr.Plan(p.nx, p.ny, p.nc, traj, "bf16x3") as plan:
+        tuned = plan.autotune(repeats=3)
+        with ClockSampler(gpu_index) as clk:
+            rate, ms, launches = _graph_rate(mr, plan, p, kspace, maps, out, 2, 1, flush, stream)
+            plan.set_timing(True)
+            plan.read_timing()
+            mr.admm_reconstruct(plan, kspace, maps, p.lam, p.beta, p.admm_iters, p.cg_iters, out=out)
+            timing = plan.read_timing()
+            plan.set_timing(False)
+    clocks = clk.summary()
+    flops_prod = useful_flops_per_product(p)
+    fwd_avg = timing["fwd_ms"] / max(1, timing["fwd_launches"])
+    adj_avg = timing["adj_ms"] / max(1, timing["adj_launches"])
+    dom = "adj" if timing["adj_ms"] >= timing["fwd_ms"] else "fwd"
+    dom_avg = adj_avg if dom == "adj" else fwd_avg
+    achieved = 3.0 * flops_prod / (dom_avg * 1e-3) / 1e12
+    peak_tf, peak_note = clock_scaled_peak(pk, clocks)
+    kern = "adj_tc_kernel" if dom == "adj" else "fwd_tc_kernel"
+    traffic, traffic_src = captured_traffic(kern, p.name)
+    return {"workload": workload_name(p), "value": rate, "unit": "recon/s", "ms_per_step": ms, "steps": 2,
+            "warmup": 1, "gpu_launches_per_step": launches, "tuning": tuned,
+            "useful_tflops": normal_ops_per_recon(p) * 2 * flops_prod / (ms * 1e-3) / 1e12,
+            "nudft": {"fwd_ms_per_launch": fwd_avg, "adj_ms_per_launch": adj_avg,
+                      "reduce_ms_per_launch": timing["red_ms"] / max(1, timing["red_launches"])},
+            "roofline": {"bound": "tensor", "kernel": kern, "achieved": achieved, "peak": peak_tf,
+                         "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": traffic,
+                         "traffic_source": traffic_src,
+                         "note": f"executed bf16 tensor flops per launch / mean launch time ({dom_avg:.4f} ms); "
+                                 f"peak = {pk_kind} {peak_note}"},
+            "clocks": clocks}
+
+
+def serve_block(args, mr, dev):
+    """A short serving run (requests sized as the batch items, Poisson
+    arrivals at 0.8 x the measured burst capacity) for the p50/p99 latency of
+    the served BF16x3 form."""
+    res = serve_measure(args, mr, dev, n_requests=args.line_serve_requests, rates=[0.8], precisions=["bf16x3"],
+                        waves=1, warmup=1)
+    head = res["bf16x3"]["sweep"][0]
+    return {"workload": f"serve{args.line_serve_requests}_poisson", "value": head["value"], "unit": "recon/s",
+            "latency_ms": {"p50": head["p50_ms"], "p99": head["p99_ms"], "max": head["max_ms"]},
+            "burst_capacity_recon_s": res["bf16x3"]["burst_capacity_recon_s"],
+            "arrival_rate_recon_s": head["arrival_rate_recon_s"], "requests": head["requests"],
+            "timing": "host wall clock, submit to image in host memory"}
 
 
 def run_batch(args, rank, world, local_rank):
@@ -568,22 +742,19 @@ def run_batch(args, rank, world, local_rank):
     }
 
 
-def run_serve(args, rank, world, local_rank):
-    """Serving loop: a stream of heterogeneous requests (sizes as the batch
-    items, each with its own phantom, maps, noise and trajectory) arriving from
-    host memory as a Poisson process, admitted under a device-memory budget
-    and run concurrently.  Per precision: a burst of the first requests
-    measures the server's capacity; then each arrival rate (a multiple of that
-    capacity) gets waves of all requests.  value = requests / (last completion
-    - first submission) at the first rate, BF16x3; latency = submission to
-    image in host memory."""
+def serve_measure(args, mr, dev, n_requests, rates, precisions, waves, warmup):
+    """Serving measurement: `n_requests` heterogeneous requests (sizes as the
+    batch items, each with its own phantom, maps, noise and trajectory)
+    arriving from host memory as a Poisson process, admitted under a
+    device-memory budget and run concurrently.  Per precision: a burst of the
+    first requests measures the server's capacity; then each arrival rate (a
+    multiple of that capacity) gets `waves` waves (the first rate) or one
+    (the others) of the requests.  Latency = submission to image in host
+    memory (host wall clock)."""
     import threading
     import torch
-    import paper_2006_14080_gb300 as mr
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    probs = [synth.serve_request(r) for r in range(args.serve_requests)]
+    probs = [synth.serve_request(r) for r in range(n_requests)]
     reqs = []
     for p in probs:
         traj = torch.from_numpy(p.traj).to(dev)
@@ -594,8 +765,6 @@ def run_serve(args, rank, world, local_rank):
                      p.maps.astype(np.complex64), p.lam, p.beta, p.admm_iters, p.cg_iters))
     torch.cuda.synchronize()
     budget = int(args.serve_budget_gb * (1 << 30))
-    rates = [float(v) for v in args.serve_rates.split(",")]
-    precisions = args.serve_precisions.split(",")
 
     def wave(srv, items, gaps):
         lat, tickets = [], []
@@ -626,37 +795,53 @@ def run_serve(args, rank, world, local_rank):
 
     results = {}
     rng = np.random.default_rng(2020)
+    for prec in precisions:
+        items = reqs if prec != "fp32" else reqs[: max(1, min(len(reqs), args.serve_fp32_requests))]
+        cap_items = items[: max(1, min(len(items), args.serve_capacity_requests))]
+        with mr.Server(budget, max_inflight=args.serve_inflight, precision=prec) as srv:
+            burst_s = 0.0
+            for _ in range(max(1, warmup if prec != "fp32" else 1)):
+                burst_s, _ = wave(srv, cap_items, [0.0] * len(cap_items))
+            capacity = len(cap_items) / burst_s
+            sweep = []
+            for k, mult in enumerate(rates):
+                nw = waves if (k == 0 and prec != "fp32") else 1
+                # the first rate takes every request; the rest of the sweep a prefix
+                wave_items = items if k == 0 or args.serve_sweep_requests <= 0 else \
+                    items[: min(len(items), args.serve_sweep_requests)]
+                total_s, lats = 0.0, []
+                for _ in range(nw):
+                    gaps = [0.0] + list(rng.exponential(1.0 / (mult * capacity), len(wave_items) - 1))
+                    t, lat = wave(srv, wave_items, gaps)
+                    total_s += t
+                    lats += lat
+                sweep.append({"rate_x_capacity": mult, "arrival_rate_recon_s": mult * capacity,
+                              "requests": len(wave_items) * nw, "value": len(wave_items) * nw / total_s,
+                              "p50_ms": pct(lats, 0.50), "p99_ms": pct(lats, 0.99), "max_ms": max(lats),
+                              "wall_s": total_s})
+            st = srv.stats()
+        results[prec] = {"burst_capacity_recon_s": capacity, "capacity_requests": len(cap_items),
+                         "sweep": sweep, "peak_resident_bytes": st["peak_resident_bytes"]}
+    return results
+
+
+def run_serve(args, rank, world, local_rank):
+    """The serving loop alone (--workload serve): value = requests / (last
+    completion - first submission) at the first arrival rate, in the first
+    precision listed."""
+    import torch
+    import paper_2006_14080_gb300 as mr
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    rates = [float(v) for v in args.serve_rates.split(",")]
+    precisions = args.serve_precisions.split(",")
     with ClockSampler(local_rank) as clk:
-        for prec in precisions:
-            items = reqs if prec != "fp32" else reqs[: max(1, min(len(reqs), args.serve_fp32_requests))]
-            cap_items = items[: max(1, min(len(items), args.serve_capacity_requests))]
-            with mr.Server(budget, max_inflight=args.serve_inflight, precision=prec) as srv:
-                burst_s = 0.0
-                for _ in range(max(1, args.warmup if prec != "fp32" else 1)):
-                    burst_s, _ = wave(srv, cap_items, [0.0] * len(cap_items))
-                capacity = len(cap_items) / burst_s
-                sweep = []
-                for k, mult in enumerate(rates):
-                    waves = args.steps if (k == 0 and prec != "fp32") else 1
-                    # the first rate takes every request; the rest of the sweep a prefix
-                    wave_items = items if k == 0 or args.serve_sweep_requests <= 0 else \
-                        items[: min(len(items), args.serve_sweep_requests)]
-                    total_s, lats = 0.0, []
-                    for _ in range(waves):
-                        gaps = [0.0] + list(rng.exponential(1.0 / (mult * capacity), len(wave_items) - 1))
-                        t, lat = wave(srv, wave_items, gaps)
-                        total_s += t
-                        lats += lat
-                    sweep.append({"rate_x_capacity": mult, "arrival_rate_recon_s": mult * capacity,
-                                  "requests": len(wave_items) * waves, "value": len(wave_items) * waves / total_s,
-                                  "p50_ms": pct(lats, 0.50), "p99_ms": pct(lats, 0.99), "max_ms": max(lats),
-                                  "wall_s": total_s})
-                st = srv.stats()
-            results[prec] = {"burst_capacity_recon_s": capacity, "capacity_requests": len(cap_items),
-                             "sweep": sweep, "peak_resident_bytes": st["peak_resident_bytes"]}
+        results = serve_measure(args, mr, dev, args.serve_requests, rates, precisions, args.steps, args.warmup)
     head = results[precisions[0]]["sweep"][0]
+    n = args.serve_requests
     return {
-        "metric": f"served ADMM recon/s, {len(reqs)} heterogeneous requests (N 64-256, 8-32 coils, 32-200 "
+        "metric": f"served ADMM recon/s, {n} heterogeneous requests (N 64-256, 8-32 coils, 32-200 "
                   "golden-angle spokes x 2N, 30 ADMM x 8 CG; own phantom, maps and trajectory each) from host "
                   f"memory, Poisson arrivals at {rates[0]} x burst capacity, {precisions[0].upper()}",
         "value": head["value"], "unit": "recon/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -665,9 +850,9 @@ def run_serve(args, rank, world, local_rank):
         "data": "synthetic (seeded per request)",
         "latency_ms": {"p50": head["p50_ms"], "p99": head["p99_ms"], "max": head["max_ms"]},
         "forms": results,
-        "config": {"workload": f"serve{len(reqs)}_poisson", "budget_bytes": budget,
+        "config": {"workload": f"serve{n}_poisson", "budget_bytes": int(args.serve_budget_gb * (1 << 30)),
                    "max_inflight": args.serve_inflight, "rates_x_capacity": rates,
-                   "fp32_requests": min(len(reqs), args.serve_fp32_requests),
+                   "fp32_requests": min(n, args.serve_fp32_requests),
                    "timing": "host wall clock, submit to image in host memory"},
         "clocks": clk.summary(),
     }
@@ -707,34 +892,95 @@ def oracle_sample(p, budget_s):
     return per_op, len(times), oracle.get_threads(), what
 
 
+def host_cpu():
+    """The host's logical CPU count and model name (from /proc/cpuinfo where
+    it names one, else the platform's processor string)."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in ln:
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+            for ln in out.splitlines():
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return os.cpu_count(), model or platform.processor() or platform.machine()
+
+
+def one_thread_normal_op_s(p):
+    """Seconds of one FP64 oracle normal operator on one host thread, from
+    the forward operator on a slice of the k-space samples (about 1e9 complex
+    MACs) scaled to forward + adjoint over all samples."""
+    import oracle
+    threads = oracle.get_threads()
+    oracle.set_threads(1)
+    try:
+        rng = np.random.default_rng(7)
+        x = synth.random_complex(rng, (p.nx, p.ny)).astype(np.complex128)
+        m = max(1, min(p.nk, int(1e9 / (p.nx * p.ny * p.nc))))
+        sub = np.ascontiguousarray(p.traj[:m])
+        t0 = time.perf_counter()
+        oracle.forward(sub, x, p.maps)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(threads)
+    return dt * 2.0 * p.nk / m, m
+
+
 def cpu_baseline(p, budget_s):
     per_op, n, threads, what = oracle_sample(p, budget_s)
+    nproc, model = host_cpu()
+    one_op, m = one_thread_normal_op_s(p)
     return {"value": 1.0 / (per_op * normal_ops_per_recon(p)), "unit": "recon/s", "cores": threads,
-            "kind": "oracle",
-            "sample": f"{n} timed calls: {what} ({workload_name(p)}), {per_op:.2f} s per normal operator, "
-                      f"scaled by {normal_ops_per_recon(p)} operators per reconstruction"}
+            "kind": "oracle", "nproc": nproc, "cpu_model": model,
+            "one_thread_value": 1.0 / (one_op * normal_ops_per_recon(p)),
+            "sample": f"{n} timed calls: {what} ({workload_name(p)}), {per_op:.2f} s per normal operator on "
+                      f"{threads} threads, scaled by {normal_ops_per_recon(p)} operators per reconstruction "
+                      f"(extrapolated); one thread: the forward operator on {m} of {p.nk} samples, "
+                      f"{one_op:.1f} s per normal operator when scaled"}
 
 
 def run_reference(args, rank):
+    """The oracle arm: each step times one FP64 normal operator (Eq. 11) of
+    the workload, the unit of work a reconstruction repeats
+    normal_ops_per_recon() times; value = recon/s extrapolated from the timed
+    operators (labelled as such), ms_per_step = the measured time per step."""
     if rank != 0:
         return None
     p = problem(args.workload if args.workload in WORKLOADS else "n128")
-    per_step = []
+    per_op_s = []
     for _ in range(args.warmup):
         oracle_sample(p, 0.0)
+    t0 = time.perf_counter()
     for _ in range(args.steps):
         per_op, _, threads, what = oracle_sample(p, 0.0)
-        per_step.append(per_op * normal_ops_per_recon(p))
-    total = sum(per_step)
-    value = args.steps / total
+        per_op_s.append(per_op)
+    wall = time.perf_counter() - t0
+    ops = normal_ops_per_recon(p)
+    value = args.steps / (sum(per_op_s) * ops)
+    nproc, model = host_cpu()
     return {
         "impl": "reference", "metric": metric_name(p), "value": value, "unit": "recon/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": workload_name(p)},
-        "cpu_baseline": {"value": value, "unit": "recon/s", "cores": threads, "kind": "oracle",
-                         "sample": f"each step: {what}, scaled by {normal_ops_per_recon(p)} operators per "
-                                   "reconstruction"},
+        "extrapolated": True,
+        "timed": f"{args.steps} steps, each one FP64 normal operator ({what}); a reconstruction is {ops} of them, "
+                 f"so value = steps / (sum of operator times x {ops})",
+        "cpu_baseline": {"value": value, "unit": "recon/s", "cores": threads, "kind": "oracle", "nproc": nproc,
+                         "cpu_model": model,
+                         "sample": f"each step: {what}, scaled by {ops} operators per reconstruction"},
         "e2e": {"value": value, "unit": "recon/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -753,6 +999,10 @@ def main():
                          "reconstruction; paper128x64 / paper1024x512: the paper's two shapes with its Table I "
                          "parameters and tolerance exits; batch64: 64 heterogeneous reconstructions in one "
                          "batched launch; serve: the serving loop under Poisson arrivals")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="single-reconstruction workloads: leave out the N=32, N=256 and serving sub-objects")
+    ap.add_argument("--line-serve-requests", type=int, default=24,
+                    help="requests of the serving sub-object of the default line")
     ap.add_argument("--batch-items", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-inflight", type=int, default=8)

@@ -16,11 +16,14 @@
 //     ordering between them) race on it; serialise them.  Every element a
 //     call reads is written earlier by the same call, so nothing needs
 //     clearing between calls.
+//   - nc must not exceed 65535 (one grid row per coil), else MRI_ERR_INVALID.
 //   - the first call on a device looks up the buffer's device address (once
 //     per device, with that device current); make that first call before any
-//     stream capture.
+//     stream capture.  The address is kept for the life of the process, so
+//     calls after a cudaDeviceReset of that device are not supported.
 //   - numerics follow the FP32 form of mri_nudft_adjoint: FP64 phase
-//     reduction, FP32 sine/cosine and FFMA products, fixed-order sums.
+//     reduction, FP32 sine/cosine and FFMA products, fixed-order two-level
+//     sums (16-sample blocks, then the running sum).
 #include <algorithm>
 #include <mutex>
 #include <string>
@@ -49,7 +52,7 @@ __device__ __forceinline__ float2 phasor(float k, int idx, int n) {
     return make_float2(c, s);
 }
 
-// part[p][c][j][i] = sum_{k in split p} conj(A_x[k][i]) y_c[k] conj(A_y[k][j]),
+// part[p][c][i][j] = sum_{k in split p} conj(A_x[k][i]) y_c[k] conj(A_y[k][j]),
 // factors formed on the fly while staging.  256 threads, 64 x 64 tile, 4 x 4 per thread.
 __global__ void __launch_bounds__(256) noalloc_adj_partials(const float *__restrict__ traj,
                                                             const float2 *__restrict__ y, float2 *__restrict__ part,
@@ -82,6 +85,11 @@ __global__ void __launch_bounds__(256) noalloc_adj_partials(const float *__restr
             Vs[s_row][s_col + q] = (ok && jj < ny) ? cconj(phasor(ky, jj, ny)) : make_float2(0.f, 0.f);
         }
         __syncthreads();
+        float2 blk[4][4];  // this stage's NBK samples, added to acc below (two-level sum)
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) blk[m][q] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int kq = 0; kq < NBK; ++kq) {
             float2 u[4], v[4];
@@ -93,37 +101,42 @@ __global__ void __launch_bounds__(256) noalloc_adj_partials(const float *__restr
             for (int m = 0; m < 4; ++m)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    acc[m][q].x = fmaf(u[m].x, v[q].x, acc[m][q].x);
-                    acc[m][q].x = fmaf(-u[m].y, v[q].y, acc[m][q].x);
-                    acc[m][q].y = fmaf(u[m].x, v[q].y, acc[m][q].y);
-                    acc[m][q].y = fmaf(u[m].y, v[q].x, acc[m][q].y);
+                    blk[m][q].x = fmaf(u[m].x, v[q].x, blk[m][q].x);
+                    blk[m][q].x = fmaf(-u[m].y, v[q].y, blk[m][q].x);
+                    blk[m][q].y = fmaf(u[m].x, v[q].y, blk[m][q].y);
+                    blk[m][q].y = fmaf(u[m].y, v[q].x, blk[m][q].y);
                 }
         }
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[m][q] = cadd(acc[m][q], blk[m][q]);
     }
-    float2 *dst = part + (((size_t)p * nc + c) * ny) * nx;
+    // image layout (j fastest), so that the combine below reads it coalesced
+    float2 *dst = part + (((size_t)p * nc + c) * nx) * ny;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int jj = j0 + tx * 4 + q;
-        if (jj >= ny) continue;
+    for (int m = 0; m < 4; ++m) {
+        const int ii = i0 + ty * 4 + m;
+        if (ii >= nx) continue;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int ii = i0 + ty * 4 + m;
-            if (ii < nx) dst[(size_t)jj * nx + ii] = acc[m][q];
+        for (int q = 0; q < 4; ++q) {
+            const int jj = j0 + tx * 4 + q;
+            if (jj < ny) dst[(size_t)ii * ny + jj] = acc[m][q];
         }
     }
 }
 
-// image[i][j] = sum_c conj(S_c[i][j]) sum_p part[p][c][j][i], fixed order.
+// image[i][j] = sum_c conj(S_c[i][j]) sum_p part[p][c][i][j], fixed order;
+// consecutive threads take consecutive pixels n = i ny + j of every array.
 __global__ void noalloc_adj_combine(const float2 *__restrict__ part, const float2 *__restrict__ maps,
                                     float2 *__restrict__ image, int nx, int ny, int nc, int ksplit) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nx * ny) return;
-    const int i = n / ny, j = n % ny;
     const size_t npix = (size_t)nx * ny;
     float2 acc = make_float2(0.f, 0.f);
     for (int c = 0; c < nc; ++c) {
         float2 w = make_float2(0.f, 0.f);
-        for (int p = 0; p < ksplit; ++p) w = cadd(w, part[(((size_t)p * nc + c) * ny + j) * nx + i]);
+        for (int p = 0; p < ksplit; ++p) w = cadd(w, part[((size_t)p * nc + c) * npix + n]);
         acc = cadd(acc, cmulc(maps[c * npix + n], w));
     }
     image[n] = acc;
@@ -170,6 +183,10 @@ extern "C" MRI_API int mri_nudft_adjoint_noalloc(int nx, int ny, int nk, int nc,
     }
     if (!traj || !kspace || !coil_maps || !image) {
         set_error("null argument");
+        return MRI_ERR_INVALID;
+    }
+    if (nc > 65535) {
+        set_error("nc = " + std::to_string(nc) + " exceeds the 65535 coils of the allocation-free entry point");
         return MRI_ERR_INVALID;
     }
     const size_t per_split_elems = (size_t)nc * nx * ny;

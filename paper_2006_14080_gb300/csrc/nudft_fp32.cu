@@ -12,6 +12,14 @@
 // partial image to part[p][c][j][i] and launch_adj_reduce sums the partials
 // in a fixed order and applies conj(S_c) (the paper's cross-core sum of
 // partial images, done on chip).
+//
+// Both products accumulate in two levels: each 16-term stage of the K loop
+// is summed into a fresh register block, which is then added to the running
+// sum.  A single sequential FP32 sum over a k-space split (hundreds of
+// samples, dominated by the large central ones of a radial trajectory)
+// carries enough rounding to move the N=32 reconstruction by ~3e-3 NRMSE
+// from the FP64 solver; with 16-sample blocks an emulation of the same
+// arithmetic lands ~8e-5 from it, for one extra add per 16 FMAs.
 #include "common.cuh"
 #include "internal.h"
 
@@ -84,6 +92,11 @@ __global__ void __launch_bounds__(256) fwd_fp32_kernel(const float2 *__restrict_
         for (int i0 = 0; i0 < nx; i0 += BK) {
             const bool more = i0 + BK < nx;
             if (more) load(i0 + BK);
+            float2 blk[4][4];  // this stage's 16 terms, added to acc below
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) blk[m][q] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int kq = 0; kq < BK; ++kq) {
                 const float4 a01 = *reinterpret_cast<const float4 *>(&As[buf][kq][ty * 4]);
@@ -98,12 +111,16 @@ __global__ void __launch_bounds__(256) fwd_fp32_kernel(const float2 *__restrict_
                 for (int m = 0; m < 4; ++m)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        acc[m][q].x = fmaf(a[m].x, b[q].x, acc[m][q].x);
-                        acc[m][q].x = fmaf(-a[m].y, b[q].y, acc[m][q].x);
-                        acc[m][q].y = fmaf(a[m].x, b[q].y, acc[m][q].y);
-                        acc[m][q].y = fmaf(a[m].y, b[q].x, acc[m][q].y);
+                        blk[m][q].x = fmaf(a[m].x, b[q].x, blk[m][q].x);
+                        blk[m][q].x = fmaf(-a[m].y, b[q].y, blk[m][q].x);
+                        blk[m][q].y = fmaf(a[m].x, b[q].y, blk[m][q].y);
+                        blk[m][q].y = fmaf(a[m].y, b[q].x, blk[m][q].y);
                     }
             }
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[m][q] = cadd(acc[m][q], blk[m][q]);
             if (more) {
                 store(buf ^ 1);
                 __syncthreads();
@@ -189,6 +206,11 @@ __global__ void __launch_bounds__(256) adj_fp32_kernel(const float2 *__restrict_
     for (int kb = kbeg; kb < kend; kb += BK) {
         const bool more = kb + BK < kend;
         if (more) load(kb + BK);
+        float2 blk[4][4];  // this stage's 16 samples, added to acc below
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) blk[m][q] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int kq = 0; kq < BK; ++kq) {
             const float4 u01 = *reinterpret_cast<const float4 *>(&Us[buf][kq][ty * 4]);
@@ -203,12 +225,16 @@ __global__ void __launch_bounds__(256) adj_fp32_kernel(const float2 *__restrict_
             for (int m = 0; m < 4; ++m)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    acc[m][q].x = fmaf(u[m].x, v[q].x, acc[m][q].x);
-                    acc[m][q].x = fmaf(-u[m].y, v[q].y, acc[m][q].x);
-                    acc[m][q].y = fmaf(u[m].x, v[q].y, acc[m][q].y);
-                    acc[m][q].y = fmaf(u[m].y, v[q].x, acc[m][q].y);
+                    blk[m][q].x = fmaf(u[m].x, v[q].x, blk[m][q].x);
+                    blk[m][q].x = fmaf(-u[m].y, v[q].y, blk[m][q].x);
+                    blk[m][q].y = fmaf(u[m].x, v[q].y, blk[m][q].y);
+                    blk[m][q].y = fmaf(u[m].y, v[q].x, blk[m][q].y);
                 }
         }
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[m][q] = cadd(acc[m][q], blk[m][q]);
         if (more) {
             store(buf ^ 1);
             __syncthreads();

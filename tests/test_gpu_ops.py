@@ -161,7 +161,7 @@ def test_tile_configurations_change_schedule_not_results(mr):
         ref_f = ref_a = None
         tried = set()
         for cpt in (1, 2, 3, 4):
-            for fs, ast in ((2, 2), (3, 3), (4, 4), (2, 4)):
+            for fs, ast in ((f, a) for f in (2, 3, 4) for a in (2, 3, 4)):
                 try:
                     plan.set_tiles(cpt, fs, ast)
                 except mr.MriError:

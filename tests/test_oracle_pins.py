@@ -453,3 +453,66 @@ def test_table1_small_workload_amplifies_any_rounding():
     e64 = nrmse(_admm_restated(p, d))
     assert 1e-5 < e64 < 1e-3
     assert nrmse(_admm_restated(p, d, vectors32=True)) > 1e-3
+
+
+def _adjoint_fp32_sum(traj, y, maps, block):
+    """The adjoint of Eq. 1 with its k-space sum carried in FP32: products
+    of FP32 factors in complex64, summed sequentially over all samples
+    (block = 0) or in sequential blocks of `block` samples whose totals are
+    then summed sequentially (two-level); coil combine in FP64."""
+    nc, nx, ny = maps.shape
+    kt = np.asarray(traj, np.float64)
+    tx = np.outer(kt[:, 0], synth.pixel_coords(nx))
+    ty = np.outer(kt[:, 1], synth.pixel_coords(ny))
+    gx = np.exp(2j * np.pi * (tx - np.rint(tx))).astype(np.complex64)  # conj(A_x)
+    gy = np.exp(2j * np.pi * (ty - np.rint(ty))).astype(np.complex64)  # conj(A_y)
+    out = np.zeros((nx, ny), np.complex128)
+    for c in range(nc):
+        terms = (gx * y[c].astype(np.complex64)[:, None])[:, :, None] * gy[:, None, :]  # [nk][nx][ny]
+        if block:
+            nb = terms.shape[0] // block
+            part = np.cumsum(terms.reshape(nb, block, nx, ny), axis=1, dtype=np.complex64)[:, -1]
+            w = np.cumsum(part, axis=0, dtype=np.complex64)[-1]
+        else:
+            w = np.cumsum(terms, axis=0, dtype=np.complex64)[-1]
+        out += np.conj(maps[c]) * w.astype(np.complex128)
+    return out
+
+
+def test_small_workload_needs_blocked_fp32_sums_in_the_adjoint():
+    # The reading behind the two-level sums of the FP32 product kernels: with
+    # FP64 CG scalars and the oracle's forward operator, an adjoint whose
+    # 1024-sample sum runs sequentially in FP32 moves the N=32 reconstruction
+    # past the 1e-3 bar; summing 16-sample blocks first keeps it well inside.
+    p = synth.config_small()
+    d = oracle.measurements(p)
+    ref = oracle.admm(p.traj, p.maps, d, p.lam, p.beta, p.admm_iters, p.cg_iters)["x"]
+    maps = p.maps.astype(np.complex128)
+    errs = {}
+    for block in (0, 16):
+        adj = lambda y: _adjoint_fp32_sum(p.traj, y, maps, block)  # noqa: E731
+        A = lambda v: adj(oracle.forward(p.traj, v, maps)) + 0.5 * p.beta * oracle.tv_adjoint(  # noqa: E731
+            oracle.tv_forward(v))
+        fhd = adj(d)
+        x = np.zeros((p.nx, p.ny), np.complex128)
+        eta = np.zeros((2, p.nx, p.ny), np.complex128)
+        for _ in range(p.admm_iters):
+            mu = oracle.shrink(oracle.tv_forward(x) + eta, p.lam / p.beta)
+            b = fhd + 0.5 * p.beta * oracle.tv_adjoint(mu - eta)
+            xn = x.copy()
+            r = b - A(xn)
+            dd = r.copy()
+            tau = np.vdot(r, r).real
+            for _ in range(p.cg_iters):
+                ad = A(dd)
+                alpha = tau / np.vdot(dd, ad).real
+                xn = xn + alpha * dd
+                r = r - alpha * ad
+                tau_next = np.vdot(r, r).real
+                dd = r + tau_next / tau * dd
+                tau = tau_next
+            eta = eta + oracle.tv_forward(xn) - mu
+            x = xn
+        errs[block] = float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+    assert errs[0] > 1e-3
+    assert errs[16] < 3e-4

@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -71,6 +72,9 @@ def test_noalloc_adjoint_matches_regular_adjoint_twice():
         got = _noalloc_adjoint(mr, nx, ny, nc, traj, kspace, maps)
         assert np.all(np.isfinite(got))
         assert _rel(got, ref) <= FP32_OP_TOL
+        # and directly against the FP64 oracle's adjoint of Eq. 1
+        exact = oracle.adjoint(traj.cpu().numpy(), kspace.cpu().numpy(), maps.cpu().numpy())
+        assert _rel(got, exact) <= FP32_OP_TOL
 
 
 def test_noalloc_adjoint_rejects_sizes_beyond_its_scratch():
@@ -81,3 +85,6 @@ def test_noalloc_adjoint_rejects_sizes_beyond_its_scratch():
     # 33 coils of 256 x 256 pixels need more than 16 MiB of partial images
     assert lib.mri_nudft_adjoint_noalloc(256, 256, 4, 33, p, p, p, p, None) == mr.MRI_ERR_INVALID
     assert b"scratch capacity" in lib.mri_last_error()
+    # more coils than grid rows: rejected up front, not at launch
+    assert lib.mri_nudft_adjoint_noalloc(1, 1, 4, 70000, p, p, p, p, None) == mr.MRI_ERR_INVALID
+    assert b"65535" in lib.mri_last_error()
