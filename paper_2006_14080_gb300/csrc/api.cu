@@ -68,7 +68,7 @@ void free_plan(mri_plan *p, cudaStream_t free_stream = nullptr) {
                     p->afwd_lo, p->badj_hi, p->badj_lo, p->bfwd_hi, p->bfwd_lo, p->afwd_t, p->badj_t,
                     p->bfwd_t,  p->bsx,     p->y,       p->part,   p->x,        p->xprev, p->r,
                     p->d,       p->ad,      p->b,       p->fhd,    p->mu,       p->eta,   p->partials,
-                    p->scal};
+                    p->scal,    p->mapsT,   p->grid_bar, p->d2,  p->r2};
     for (void *q : bufs)
         if (q) {
             if (p->pool)
@@ -182,6 +182,29 @@ static cudaError_t op_normal(mri_plan *p, const float2 *src, const float2 *maps,
     return e;
 }
 
+// The solver's forward product of the operand it has written (no operand kernel).
+static cudaError_t solver_forward(mri_plan *p, int skip, cudaStream_t s) {
+    const bool timed = timing_arm(p);
+    cudaError_t e = is_tc_precision(p->precision) ? launch_fwd_tc(p, nullptr, nullptr, p->y, p->nk_pad, skip, s)
+                                                  : launch_fwd_fp32(p, nullptr, nullptr, p->y, p->nk_pad, skip, s);
+    if (timed) timing_disarm(p, p->ev_fwd);
+    return e;
+}
+
+// One fused CG step (finishes the adjoint, then Alg. 2's updates); timed
+// with the reductions.
+static cudaError_t solver_cg_step(mri_plan *p, float half_beta, int it, cudaStream_t s) {
+    const bool timed = timing_arm(p);
+    if (timed) cudaEventRecord(p->t_ev0, s);
+    cudaError_t e = launch_cg_step(p, half_beta, it, s);
+    p->launches += 1;
+    if (timed) {
+        cudaEventRecord(p->t_ev1, s);
+        timing_disarm(p, p->ev_red);
+    }
+    return e;
+}
+
 }  // namespace mri
 
 using namespace mri;
@@ -274,14 +297,16 @@ int plan_create(mri_plan **out, int nx, int ny, int nk, int nc, const float *tra
     }
     if (rc == MRI_OK) rc = dev_alloc(p, &p->y, (size_t)nc * p->nk_pad);
     if (rc == MRI_OK) rc = dev_alloc(p, &p->part, (size_t)p->ksplit * nc * ny * p->nx_pad);
-    float2 **img_bufs[] = {&p->x, &p->xprev, &p->r, &p->d, &p->ad, &p->b, &p->fhd};
+    float2 **img_bufs[] = {&p->x, &p->xprev, &p->r, &p->r2, &p->d, &p->d2, &p->ad, &p->b, &p->fhd};
     for (float2 **q : img_bufs)
         if (rc == MRI_OK) rc = dev_alloc(p, q, npix);
     if (rc == MRI_OK) rc = dev_alloc(p, &p->mu, 2 * npix);
     if (rc == MRI_OK) rc = dev_alloc(p, &p->eta, 2 * npix);
+    if (rc == MRI_OK) rc = dev_alloc(p, &p->mapsT, (size_t)nc * ny * p->nx_pad);
+    if (rc == MRI_OK) rc = dev_alloc(p, &p->grid_bar, 2);
     // one slot pair per block of the largest reducing grid (element-wise
     // kernels use at most 1024 blocks, the adjoint reduction one per 32x32 tile)
-    p->partials_cap = 2 * std::max(1024, ceil_div(nx, 32) * ny);
+    p->partials_cap = 3 * std::max(1024, ceil_div(nx, 32) * ny);
     if (rc == MRI_OK) rc = dev_alloc(p, &p->partials, (size_t)p->partials_cap);
     if (rc == MRI_OK) rc = dev_alloc(p, &p->scal, 1);
     if (rc != MRI_OK) {
@@ -307,6 +332,9 @@ int plan_create(mri_plan **out, int nx, int ny, int nk, int nc, const float *tra
     if (e == cudaSuccess && p->axQ) e = cudaMemsetAsync(p->axQ, 0, (size_t)16 * p->nk_pad * 8, s);
     if (e == cudaSuccess && p->ayT) e = cudaMemsetAsync(p->ayT, 0, (size_t)ny * p->nk_pad * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->scal, 0, sizeof(DevScalars), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->grid_bar, 0, 2 * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->mapsT, 0, (size_t)nc * ny * p->nx_pad * sizeof(float2), s);
+    p->cg_grid = cg_step_grid(p);
     if (e == cudaSuccess && is_tc_precision(precision)) {
         rc = tc_make_tensor_maps(p);
         int cpt = 0, fs = 0, as = 0;
@@ -401,8 +429,10 @@ MRI_API size_t mri_plan_estimate_bytes(int nx, int ny, int nk, int nc, int preci
         t.ksplit = choose_ksplit_fp32(&t, &per);
         bytes += c64 * ((size_t)nk * nx + (size_t)nk * ny + (size_t)nc * npix);
     }
-    bytes += c64 * ((size_t)nc * t.nk_pad + (size_t)t.ksplit * nc * ny * t.nx_pad + 7 * npix + 4 * npix);
-    bytes += sizeof(double) * (size_t)(2 * std::max(1024, ceil_div(nx, 32) * ny));
+    bytes += c64 * ((size_t)nc * t.nk_pad + (size_t)t.ksplit * nc * ny * t.nx_pad + 9 * npix + 4 * npix +
+                    (size_t)nc * ny * t.nx_pad);
+    bytes += 2 * sizeof(unsigned);
+    bytes += sizeof(double) * (size_t)(3 * std::max(1024, ceil_div(nx, 32) * ny));
     bytes += sizeof(DevScalars);
     return bytes;
 }
@@ -464,7 +494,12 @@ MRI_API int mri_soft_threshold(int n, float t, const mri_c64 *in, mri_c64 *out, 
 
 }  // extern "C"
 
-// Enqueue the whole reconstruction (Alg. 4 with Alg. 2) on s.
+// Enqueue the whole reconstruction (Alg. 4 with Alg. 2) on s.  The solver
+// works on the plan's transposed copies of the image-sized state (admm.cu):
+// the coil maps and any saved state are transposed in first, the image and
+// the final dual variable out at the end.  Per CG step: the forward product
+// (its operand written by the kernel before it), the adjoint product, and
+// one cooperative kernel that finishes the adjoint and takes the CG step.
 int mri::enqueue_admm(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in, const mri_admm_params *prm,
                       mri_c64 *image_out, double *objective_hist, double *alpha_hist, cudaStream_t s,
                       const AdmmWarm &warm) {
@@ -486,38 +521,40 @@ int mri::enqueue_admm(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps
     } while (0)
 
     KERNEL(launch_admm_reset(p, prm->atol, prm->rtol, s));
+    KERNEL(launch_transpose(maps, p->mapsT, p->nx, p->ny, p->nc, s, p->nx_pad));
     // x^0 = 0 and eta^0 = 0 (Alg. 4), or a saved state to resume from
     if (warm.x0)
-        STEP(cudaMemcpyAsync(p->x, warm.x0, npix * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+        KERNEL(launch_transpose((const float2 *)warm.x0, p->x, p->nx, p->ny, 1, s));
     else
         STEP(cudaMemsetAsync(p->x, 0, npix * sizeof(float2), s));
     if (warm.eta0)
-        STEP(cudaMemcpyAsync(p->eta, warm.eta0, 2 * npix * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+        KERNEL(launch_transpose((const float2 *)warm.eta0, p->eta, p->nx, p->ny, 2, s));
     else
         STEP(cudaMemsetAsync(p->eta, 0, 2 * npix * sizeof(float2), s));
     // F^H d, once per reconstruction (Section IV-C: the right-hand side stays
     // fixed through the CG iterations)
     STEP(op_adjoint_partials(p, kspace, kSkipNever, s));
-    KERNEL(launch_adj_reduce(p, maps, p->fhd, ReduceEpilogue(), s));
+    KERNEL(launch_fhd(p, s));
     for (int m = 0; m < prm->admm_iters; ++m) {
-        KERNEL(launch_admm_mu(p, thresh, s));        // Eq. 8
-        KERNEL(launch_admm_rhs(p, half_beta, s));    // Eq. 12
-        STEP(op_normal(p, p->x, maps, p->ad, half_beta, false, kSkipAdmm, s));  // A x0
-        KERNEL(launch_cg_init(p, s));
+        KERNEL(launch_mu_rhs(p, thresh, half_beta, s));  // Eq. 8 (mu), Eq. 12 (b), operand of x
+        // A x0 and the start of Alg. 2
+        STEP(solver_forward(p, kSkipAdmm, s));
+        STEP(op_adjoint_partials(p, p->y, kSkipAdmm, s));
+        KERNEL(launch_cg_init(p, half_beta, s));
         for (int it = 0; it < prm->cg_iters; ++it) {
-            if (it > 0) KERNEL(launch_cg_direction(p, s));
-            STEP(op_normal(p, p->d, maps, p->ad, half_beta, true, kSkipCg, s));  // A d, alpha
-            KERNEL(launch_cg_update(p, s));
+            STEP(solver_forward(p, kSkipCg, s));                // F d (operand written by the kernel before)
+            STEP(op_adjoint_partials(p, p->y, kSkipCg, s));     // F^H F d, partial images
+            STEP(solver_cg_step(p, half_beta, it, s));          // A d, alpha, x, r, beta, d, operand of d
         }
-        KERNEL(launch_admm_dual(p, alpha_hist, m, s));  // Eq. 8 (dual), Alg. 4 relative change
-        if (objective_hist) {
-            STEP(op_forward(p, p->x, maps, p->y, p->nk_pad, kSkipStep, s));
+        const bool obj = objective_hist != nullptr;
+        KERNEL(launch_dual(p, obj, alpha_hist, m, s));  // Eq. 8 (dual), Alg. 4 relative change
+        if (obj) {
+            STEP(solver_forward(p, kSkipStep, s));
             KERNEL(launch_objective(p, kspace, prm->lambda, objective_hist, m, s));
         }
     }
-    STEP(cudaMemcpyAsync(image_out, p->x, npix * sizeof(float2), cudaMemcpyDeviceToDevice, s));
-    if (warm.eta_out)
-        STEP(cudaMemcpyAsync(warm.eta_out, p->eta, 2 * npix * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    KERNEL(launch_transpose(p->x, (float2 *)image_out, p->ny, p->nx, 1, s));
+    if (warm.eta_out) KERNEL(launch_transpose(p->eta, (float2 *)warm.eta_out, p->ny, p->nx, 2, s));
 #undef KERNEL
 #undef STEP
     return MRI_OK;

@@ -26,6 +26,17 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t *>(&v); }
+
+// hi/lo split of a pair of FP32 values into packed bf16x2 words (a in the low
+// half): hi = bf16(v), lo = bf16(v - hi), both rounded to nearest even.
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat162 h = __float22bfloat162_rn(make_float2(a, b));
+    const float2 hf = __bfloat1622float2(h);
+    hi = bf2_bits(h);
+    lo = bf2_bits(__float22bfloat162_rn(make_float2(a - hf.x, b - hf.y)));
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -77,16 +88,18 @@ __device__ __forceinline__ bool grid_reduce_last(const double (&part)[NV], doubl
     __syncthreads();
     if (!is_last) return false;
     __threadfence();
-    // every thread of the last block adds a fixed strided subset of the
-    // partials, then the block sums the per-thread values in a fixed order
-    __shared__ double scratch[32];
-    const int nthreads = blockDim.x * blockDim.y;
+    // warp 0 of the last block adds the partials: lane l takes blocks l,
+    // l + 32, ... in order, then the lanes are combined in a fixed order (the
+    // other warps take no part: FP64 adds are slow on this GPU)
     double s[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        double v = 0.0;
-        for (int b = tid; b < nblocks; b += nthreads) v += __ldcg(&partials[(size_t)b * NV + q]);
-        s[q] = block_sum(v, scratch);
+    for (int q = 0; q < NV; ++q) s[q] = 0.0;
+    if (tid < 32) {
+        for (int b = tid; b < nblocks; b += 32)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) s[q] += __ldcg(&partials[(size_t)b * NV + q]);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) s[q] = warp_sum(s[q]);
     }
     if (tid == 0) {
         fin(s);

@@ -115,16 +115,23 @@ struct mri_plan {
     // operator workspace
     float2 *bsx = nullptr;    // [nc][nx][ny] S_c . x (FP32 path)
     float2 *y = nullptr;      // [nc][nk_pad] k-space workspace (padding stays zero)
-    float2 *part = nullptr;   // [ksplit][nc][ny][nx_pad] adjoint partial images
+    // adjoint partial images part[c][j][ig][p][64]: pixel i = 64 ig + (i % 64)
+    // fastest, then the k-space split p, the 64-pixel group ig (nx_pad / 64 of
+    // them), the column j and the coil, so that the splits of one coil, column
+    // and pixel group are contiguous for the fixed-order sum
+    float2 *part = nullptr;
     int ksplit = 1;           // k-space splits of the adjoint product
     int ksplit_blocks = 0;    // K blocks per split (tensor path) or samples per split (FP32)
 
-    // solver state
-    float2 *x = nullptr, *xprev = nullptr, *r = nullptr, *d = nullptr, *ad = nullptr;
-    float2 *b = nullptr, *fhd = nullptr;                 // [nx][ny]
-    float2 *mu = nullptr, *eta = nullptr;                // [2][nx][ny]
+    // solver state, in the transposed layout v[j][i] (pixel (i, j) at j * nx + i)
+    float2 *x = nullptr, *xprev = nullptr, *r = nullptr, *r2 = nullptr, *d = nullptr, *d2 = nullptr, *ad = nullptr;
+    float2 *b = nullptr, *fhd = nullptr;                 // [ny][nx]
+    float2 *mu = nullptr, *eta = nullptr;                // [2][ny][nx]
+    float2 *mapsT = nullptr;                             // [nc][ny][nx_pad]: the coil maps of the reconstruction
     double *partials = nullptr;                          // grid-reduction partials
     int partials_cap = 0;                                // doubles
+    unsigned *grid_bar = nullptr;                        // [2]: the CG step's grid barrier (count, generation)
+    int cg_grid = 0;                                     // blocks of the cooperative CG step
     mri::DevScalars *scal = nullptr;
 
     size_t bytes = 0;
@@ -205,12 +212,15 @@ void set_error(const std::string &msg);
 // factors.cu
 cudaError_t launch_factors(mri_plan *p, const float *traj, cudaStream_t s);
 
-// nudft_fp32.cu -- forward writes kspace[c * ld + k]; adjoint reads p->y
+// nudft_fp32.cu -- forward writes kspace[c * ld + k] (image == nullptr: the
+// operand S_c . v is already in p->bsx, transposed, written by the solver);
+// adjoint reads p->y
 cudaError_t launch_fwd_fp32(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace, int ld,
                             int skip, cudaStream_t s);
 cudaError_t launch_adj_fp32(mri_plan *p, int skip, cudaStream_t s);
 
-// nudft_tc.cu -- same conventions
+// nudft_tc.cu -- same conventions (image == nullptr: the operand is already
+// in bfwd_hi/lo or bfwd_t, written by the solver)
 bool tc_supported(const mri_plan *p, std::string *why);
 int tc_plan_tiling(mri_plan *p);       // tile shapes and k-space splits; MRI_* status
 int tc_make_tensor_maps(mri_plan *p);  // TMA descriptors of the allocated operands; MRI_* status
@@ -237,14 +247,22 @@ cudaError_t launch_adj_reduce(mri_plan *p, const float2 *maps, float2 *out, cons
 cudaError_t launch_tv_forward(int nx, int ny, const float2 *x, float2 *g, cudaStream_t s);
 cudaError_t launch_tv_adjoint(int nx, int ny, const float2 *g, float2 *x, cudaStream_t s);
 cudaError_t launch_shrink(int n, float t, const float2 *in, float2 *out, cudaStream_t s);
-cudaError_t launch_admm_mu(mri_plan *p, float thresh, cudaStream_t s);
-cudaError_t launch_admm_rhs(mri_plan *p, float half_beta, cudaStream_t s);
-cudaError_t launch_cg_init(mri_plan *p, cudaStream_t s);
-cudaError_t launch_cg_update(mri_plan *p, cudaStream_t s);
-cudaError_t launch_cg_direction(mri_plan *p, cudaStream_t s);
-cudaError_t launch_admm_dual(mri_plan *p, double *alpha_hist, int m, cudaStream_t s);
+
+// admm.cu -- the reconstruction's kernels, on the plan's transposed state
+// dst[b][c][r] = src[b][r][c] for `planes` planes of rows x cols complex
+// values; destination rows ld_dst apart (0: rows)
+cudaError_t launch_transpose(const float2 *src, float2 *dst, int rows, int cols, int planes, cudaStream_t s,
+                             int ld_dst = 0);
+cudaError_t launch_admm_reset(mri_plan *p, double atol, double rtol, cudaStream_t s);
+cudaError_t launch_fhd(mri_plan *p, cudaStream_t s);  // fhd from the adjoint's partial images
+cudaError_t launch_mu_rhs(mri_plan *p, float thresh, float half_beta, cudaStream_t s);
+cudaError_t launch_cg_init(mri_plan *p, float half_beta, cudaStream_t s);
+// cooperative; step `it` of a CG solve reads the residual and direction
+// from r, d (it even) or r2, d2 (odd) and leaves the next ones in the others
+cudaError_t launch_cg_step(mri_plan *p, float half_beta, int it, cudaStream_t s);
+cudaError_t launch_dual(mri_plan *p, bool operand, double *alpha_hist, int m, cudaStream_t s);
 cudaError_t launch_objective(mri_plan *p, const float2 *kspace, float lambda, double *obj_hist, int m,
                              cudaStream_t s);
-cudaError_t launch_admm_reset(mri_plan *p, double atol, double rtol, cudaStream_t s);
+int cg_step_grid(const mri_plan *p);  // co-resident blocks of the cooperative CG step
 
 }  // namespace mri

@@ -9,7 +9,8 @@
 // Adjoint:
 //   W_c = A_x^H diag(y_c) conj(A_y)            ([nx x nk] x [nk x ny])
 // split over `ksplit` contiguous ranges of samples; each range writes a
-// partial image to part[p][c][j][i] and launch_adj_reduce sums the partials
+// partial image to part[c][j][ig][p][64] (the layout of the tensor-core
+// adjoint, pixel i = 64 ig + (i % 64)) and launch_adj_reduce sums the partials
 // in a fixed order and applies conj(S_c) (the paper's cross-core sum of
 // partial images, done on chip).
 //
@@ -42,8 +43,8 @@ __global__ void coil_product_kernel(const float2 *__restrict__ x, const float2 *
 
 __global__ void __launch_bounds__(256) fwd_fp32_kernel(const float2 *__restrict__ ax, const float2 *__restrict__ ay,
                                                        const float2 *__restrict__ bsx, float2 *__restrict__ y,
-                                                       int y_ld, int nx, int ny, int nk, const DevScalars *sc,
-                                                       int skip) {
+                                                       int y_ld, int nx, int ny, int nk, int b_transposed,
+                                                       const DevScalars *sc, int skip) {
     if (should_skip(sc, skip)) return;
     __shared__ __align__(16) float2 As[2][BK][BM];  // As[k][m] = A_x[k0+m][i0+k]
     __shared__ __align__(16) float2 Bs[2][BK][BN];  // Bs[k][n] = B_c[i0+k][j0+n]
@@ -75,7 +76,8 @@ __global__ void __launch_bounds__(256) fwd_fp32_kernel(const float2 *__restrict_
                 const int kk = k0 + a_row, ii = i0 + a_col + q;
                 ra[q] = (kk < nk && ii < nx) ? ax[(size_t)kk * nx + ii] : make_float2(0.f, 0.f);
                 const int bi = i0 + b_row, bj = j0 + b_col + q;
-                rb[q] = (bi < nx && bj < ny) ? B[(size_t)bi * ny + bj] : make_float2(0.f, 0.f);
+                rb[q] = (bi < nx && bj < ny) ? B[b_transposed ? (size_t)bj * nx + bi : (size_t)bi * ny + bj]
+                                             : make_float2(0.f, 0.f);
             }
         };
         auto store = [&](int buf) {
@@ -154,11 +156,12 @@ __global__ void __launch_bounds__(256) fwd_fp32_kernel(const float2 *__restrict_
     }
 }
 
-// part[p][c][j][i] = sum_{k in split p} conj(A_x[k][i]) y_c[k] conj(A_y[k][j])
+// part[c][j][i / 64][p][i % 64] = sum_{k in split p} conj(A_x[k][i]) y_c[k] conj(A_y[k][j])
 __global__ void __launch_bounds__(256) adj_fp32_kernel(const float2 *__restrict__ ax, const float2 *__restrict__ ay,
                                                        const float2 *__restrict__ y, float2 *__restrict__ part,
                                                        int y_ld, int nx, int ny, int nk, int nc, int nx_pad,
-                                                       int samples_per_split, const DevScalars *sc, int skip) {
+                                                       int ksplit, int samples_per_split, const DevScalars *sc,
+                                                       int skip) {
     if (should_skip(sc, skip)) return;
     __shared__ __align__(16) float2 Us[2][BK][BM];  // Us[k][m] = conj(A_x[k][i0+m]) y_c[k]
     __shared__ __align__(16) float2 Vs[2][BK][BN];  // Vs[k][n] = conj(A_y[k][j0+n])
@@ -241,8 +244,9 @@ __global__ void __launch_bounds__(256) adj_fp32_kernel(const float2 *__restrict_
             buf ^= 1;
         }
     }
-    // write the partial image, transposed: part[p][c][j][i]
-    float2 *dst = part + (((size_t)p * nc + c) * ny) * nx_pad;
+    // write the partial image: the tile's 64 rows i are one 64-pixel group
+    const size_t js = (size_t)(nx_pad / 64) * ksplit * 64;
+    float2 *dst = part + (size_t)c * ny * js + (size_t)(i0 >> 6) * ksplit * 64 + (size_t)p * 64;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int jj = j0 + tx * 4 + q;
@@ -250,7 +254,7 @@ __global__ void __launch_bounds__(256) adj_fp32_kernel(const float2 *__restrict_
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int ii = i0 + ty * 4 + m;
-            if (ii < nx) dst[(size_t)jj * nx_pad + ii] = acc[m][q];
+            if (ii < nx) dst[(size_t)jj * js + (ii & 63)] = acc[m][q];
         }
     }
 }
@@ -260,12 +264,16 @@ __global__ void __launch_bounds__(256) adj_fp32_kernel(const float2 *__restrict_
 cudaError_t launch_fwd_fp32(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace, int ld,
                             int skip, cudaStream_t s) {
     const int npix = p->nx * p->ny;
-    coil_product_kernel<<<ceil_div(npix, 256), 256, 0, s>>>(image, maps, p->bsx, npix, p->nc, p->scal, skip);
+    if (image) {  // else the solver has written S_c . v to bsx, transposed
+        coil_product_kernel<<<ceil_div(npix, 256), 256, 0, s>>>(image, maps, p->bsx, npix, p->nc, p->scal, skip);
+        p->launches += 1;
+    }
     dim3 grid(ceil_div(p->nk, BM), p->nc);
     timing_begin(p, s);
-    fwd_fp32_kernel<<<grid, 256, 0, s>>>(p->ax, p->ay, p->bsx, kspace, ld, p->nx, p->ny, p->nk, p->scal, skip);
+    fwd_fp32_kernel<<<grid, 256, 0, s>>>(p->ax, p->ay, p->bsx, kspace, ld, p->nx, p->ny, p->nk, image ? 0 : 1,
+                                         p->scal, skip);
     timing_end(p, s);
-    p->launches += 2;
+    p->launches += 1;
     return cudaGetLastError();
 }
 
@@ -273,7 +281,7 @@ cudaError_t launch_adj_fp32(mri_plan *p, int skip, cudaStream_t s) {
     dim3 grid(ceil_div(p->nx, BM) * ceil_div(p->ny, BN), p->nc, p->ksplit);
     timing_begin(p, s);
     adj_fp32_kernel<<<grid, 256, 0, s>>>(p->ax, p->ay, p->y, p->part, p->nk_pad, p->nx, p->ny, p->nk, p->nc,
-                                         p->nx_pad, p->ksplit_blocks, p->scal, skip);
+                                         p->nx_pad, p->ksplit, p->ksplit_blocks, p->scal, skip);
     timing_end(p, s);
     p->launches += 1;
     return cudaGetLastError();

@@ -106,7 +106,10 @@ struct FwdParams {
 };
 
 struct AdjParams {
-    float2 *part;  // [ksplit][nc][ny][nx_pad]
+    // partial images, part[c][j][ig][p][64] (pixel i = 64 ig + (i % 64) fastest,
+    // then the k-space split p, the 64-pixel group ig, the column j, the coil)
+    float2 *part;
+    int ksplit, n_ig;
     // ny_pad here is the tile width (the UMMA N, at most 256).  An image wider
     // than that is covered by one launch per 256-column part: part points at
     // the part's first column, b_row0 is its first conj(A_y) row and ny_lim
@@ -130,16 +133,6 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
 __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity) {
     volatile int local = 0;
     mbar_wait(bar, parity, &local, kDrainLimitNs);
-}
-
-__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t *>(&v); }
-
-// hi/lo split of a pair of FP32 values into packed bf16x2 words (a in the low half).
-__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo) {
-    const __nv_bfloat162 h = __float22bfloat162_rn(make_float2(a, b));
-    const float2 hf = __bfloat1622float2(h);
-    hi = bf2_bits(h);
-    lo = bf2_bits(__float22bfloat162_rn(make_float2(a - hf.x, b - hf.y)));
 }
 
 // For U = (ur, ui): the Re-row word (ur, -ui) and the Im-row word (ui, ur) of
@@ -795,24 +788,25 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
             const int c = m % P.nc, ib = m / P.nc;
             const int i = ib * kPx + ii;
             const uint32_t col0 = (uint32_t)(a * P.ny_pad);
+            const size_t js = (size_t)P.n_ig * P.ksplit * 64;  // between columns j of the partials
+            float2 *pix = P.part + (size_t)c * P.ny * js + (size_t)(i >> 6) * P.ksplit * 64 + (size_t)p * 64 + (i & 63);
             if constexpr (kPx128) {
                 // columns 2j, 2j+1 = Re, Im of image column j (UMMA N = 2 ny_pad, a multiple of 32)
-                float2 *dst = P.part + ((size_t)p * P.nc + c) * P.ny * P.nx_pad + i;
                 for (int jc = 0; jc < P.ny_pad; jc += 32) {
                     float v[32];
                     tmem_ld_32cols(tmem_base + lane_base + col0 + jc, v);
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         const int j = jc / 2 + q;
-                        if (j < P.ny_lim) dst[(size_t)j * P.nx_pad] = make_float2(v[2 * q], v[2 * q + 1]);
+                        if (j < P.ny_lim) pix[(size_t)j * js] = make_float2(v[2 * q], v[2 * q + 1]);
                     }
                 }
                 fence_before_sync();
                 mbar_arrive(tempty0 + 8 * a);
                 continue;
             }
-            float *dst = reinterpret_cast<float *>(P.part + ((size_t)p * P.nc + c) * P.ny * P.nx_pad) + 2 * i + o;
-            const size_t jstride = 2 * (size_t)P.nx_pad;
+            float *dst = reinterpret_cast<float *>(pix) + o;
+            const size_t jstride = 2 * js;
             int jc = 0;
             for (; jc + 32 <= P.ny_pad; jc += 32) {
                 float v[32];
@@ -1131,14 +1125,17 @@ int tc_set_tiles(mri_plan *p, int cpt, int fwd_stages, int adj_stages) {
 cudaError_t launch_fwd_tc(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace, int ld, int skip,
                           cudaStream_t s) {
     const bool t = p->precision == MRI_TF32;
-    dim3 og(ceil_div(p->nx, 32), ceil_div(p->ny, 32), p->nc);
-    if (t)
-        fwd_operand_kernel<true><<<og, dim3(32, 8), 0, s>>>(image, maps, nullptr, nullptr, (uint2 *)p->bfwd_t, p->nx,
-                                                            p->ny, p->ny_pad, p->kx, p->scal, skip);
-    else
-        fwd_operand_kernel<false><<<og, dim3(32, 8), 0, s>>>(image, maps, (uint32_t *)p->bfwd_hi,
-                                                             (uint32_t *)p->bfwd_lo, nullptr, p->nx, p->ny,
-                                                             p->ny_pad, p->kx, p->scal, skip);
+    if (image) {  // else the solver has written the operand already
+        dim3 og(ceil_div(p->nx, 32), ceil_div(p->ny, 32), p->nc);
+        if (t)
+            fwd_operand_kernel<true><<<og, dim3(32, 8), 0, s>>>(image, maps, nullptr, nullptr, (uint2 *)p->bfwd_t,
+                                                                p->nx, p->ny, p->ny_pad, p->kx, p->scal, skip);
+        else
+            fwd_operand_kernel<false><<<og, dim3(32, 8), 0, s>>>(image, maps, (uint32_t *)p->bfwd_hi,
+                                                                 (uint32_t *)p->bfwd_lo, nullptr, p->nx, p->ny,
+                                                                 p->ny_pad, p->kx, p->scal, skip);
+        p->launches += 1;
+    }
     FwdParams P;
     P.y = kspace;
     P.y_ld = ld;
@@ -1168,13 +1165,15 @@ cudaError_t launch_fwd_tc(mri_plan *p, const float2 *image, const float2 *maps, 
                                                              p->tm_bfwd_lo, p->tm_ayT, P);
     cudaError_t e = cudaGetLastError();
     timing_end(p, s);
-    p->launches += 2;
+    p->launches += 1;
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
     AdjParams P;
     P.part = p->part;
+    P.ksplit = p->ksplit;
+    P.n_ig = p->nx_pad / 64;
     P.nx = p->nx;
     P.ny = p->ny;
     P.ny_pad = p->adj_block_n;  // the tile width
@@ -1198,7 +1197,7 @@ cudaError_t launch_adj_tc(mri_plan *p, int skip, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     for (int part = 0; part < n_parts && e == cudaSuccess; ++part) {
         const int j0 = part * p->adj_block_n;  // n_parts > 1 only in the row-pair form
-        P.part = p->part + (size_t)j0 * p->nx_pad;  // column j0 of every (split, coil) plane
+        P.part = p->part + (size_t)j0 * P.n_ig * p->ksplit * 64;  // column j0 of every coil's partials
         P.ny_lim = p->ny - j0;
         P.b_row0 = j0;
         adj_kernel_for(p)<<<grid, kAdjThreads, smem, s>>>(p->tm_badj_hi, p->tm_badj_lo, p->tm_axT,

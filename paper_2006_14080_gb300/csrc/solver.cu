@@ -1,10 +1,10 @@
-// Image-space kernels of the reconstruction: the fixed-order reduction that
-// finishes the adjoint (sum over k-space splits, coil combination, optional
-// (beta/2) Theta^H Theta term and CG dot product), the finite-difference
-// transform Theta and its transpose, the soft threshold (Eq. 9), and the
-// CG (Alg. 2) and ADMM (Alg. 4, Eq. 6-12) vector updates with FP64 scalar
-// reductions.  All image-sized arrays are [nx][ny] complex64; the TV fields
-// are [2][nx][ny].
+// Image-space kernels of the operator entry points: the fixed-order
+// reduction that finishes the adjoint (sum over k-space splits, coil
+// combination, optional (beta/2) Theta^H Theta term and CG dot product), the
+// finite-difference transform Theta and its transpose, and the soft
+// threshold (Eq. 9).  All image-sized arrays are in the ABI layout [nx][ny]
+// complex64; the TV fields are [2][nx][ny].  The reconstruction's own
+// kernels (Alg. 2 and 4) are in admm.cu.
 #include "common.cuh"
 #include "internal.h"
 
@@ -41,7 +41,7 @@ __device__ __forceinline__ float2 theta_h_theta_at(const float2 *p, int i, int j
     return cadd(csub(gx_up, gx_here), csub(gy_left, gy_here));
 }
 
-// out[i][j] = sum_c conj(S_c[i][j]) sum_p part[p][c][j][i]  (+ half_beta Theta^H Theta tv_src)
+// out[i][j] = sum_c conj(S_c[i][j]) sum_p part[c][j][i / 64][p][i % 64]  (+ half_beta Theta^H Theta tv_src)
 // and optionally Re<dot_src, out> -> alpha = tau / dot.  Block (32, G),
 // G = min(nc, 16): it covers the 64 consecutive pixels i of one column j,
 // two per lane (one 16-byte load of each partial row); thread row ty takes
@@ -63,9 +63,11 @@ __global__ void __launch_bounds__(32 * kReduceGroups, 2)
     const size_t npix = (size_t)nx * ny;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i0 < nx) {
-        const size_t pstride = (size_t)nc * ny * nx_pad / 2;  // float4 units between k-space splits
+        const size_t pstride = 32;  // float4 units between k-space splits (64 pixels)
+        const int n_ig = nx_pad / 64;
         for (int c = ty; c < nc; c += G) {
-            const float4 *src = reinterpret_cast<const float4 *>(part + ((size_t)c * ny + j) * nx_pad + i0);
+            const float4 *src = reinterpret_cast<const float4 *>(
+                part + (((size_t)c * ny + j) * n_ig + blockIdx.x) * ksplit * 64 + 2 * tx);
             // w[e] sums the splits p = e (mod 4) in increasing order
             float4 w[4];
 #pragma unroll
@@ -143,176 +145,6 @@ __global__ void shrink_kernel(int n, float t, const float2 *in, float2 *out) {
     if (q < n) out[q] = soft_threshold(in[q], t);
 }
 
-// mu = S_t(Theta x + eta); xprev = x; opens a new x-update (cg_done = 0).
-__global__ void admm_mu_kernel(int nx, int ny, const float2 *__restrict__ x, const float2 *__restrict__ eta,
-                               float2 *__restrict__ mu, float2 *__restrict__ xprev, float t, DevScalars *sc) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (sc->admm_done) {
-        if (n == 0) sc->step_active = 0;
-        return;
-    }
-    if (n == 0) {
-        sc->cg_done = 0;
-        sc->step_active = 1;
-    }
-    if (n >= nx * ny) return;
-    const size_t npix = (size_t)nx * ny;
-    const int i = n / ny, j = n % ny;
-    float2 gx, gy;
-    theta_at(x, i, j, nx, ny, gx, gy);
-    mu[n] = soft_threshold(cadd(gx, eta[n]), t);
-    mu[npix + n] = soft_threshold(cadd(gy, eta[npix + n]), t);
-    xprev[n] = x[n];
-}
-
-// b = F^H d + half_beta Theta^H (mu - eta)   (Eq. 12)
-__global__ void admm_rhs_kernel(int nx, int ny, const float2 *__restrict__ fhd, const float2 *__restrict__ mu,
-                                const float2 *__restrict__ eta, float2 *__restrict__ b, float half_beta,
-                                const DevScalars *sc) {
-    if (sc->admm_done) return;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= nx * ny) return;
-    const size_t npix = (size_t)nx * ny;
-    const int i = n / ny, j = n % ny;
-    // Theta^H of the field pair (mu - eta), evaluated from its four neighbours
-    auto diff = [&](int f, int ii, int jj) -> float2 {
-        if (ii < 0 || jj < 0) return make_float2(0.f, 0.f);
-        const size_t q = (size_t)f * npix + (size_t)ii * ny + jj;
-        return csub(mu[q], eta[q]);
-    };
-    float2 t = cadd(csub(diff(0, i - 1, j), diff(0, i, j)), csub(diff(1, i, j - 1), diff(1, i, j)));
-    const float2 f = fhd[n];
-    b[n] = make_float2(fmaf(half_beta, t.x, f.x), fmaf(half_beta, t.y, f.y));
-}
-
-// r = b - A x, d = r, tau = ||r||^2 (Alg. 2 start, A x already in ad)
-__global__ void cg_init_kernel(int npix, const float2 *__restrict__ b, const float2 *__restrict__ ax,
-                               float2 *__restrict__ r, float2 *__restrict__ d, DevScalars *sc, double *partials) {
-    if (sc->admm_done) return;
-    __shared__ double red[32];
-    double s = 0.0;
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < npix; n += gridDim.x * blockDim.x) {
-        const float2 v = csub(b[n], ax[n]);
-        r[n] = v;
-        d[n] = v;
-        s += (double)v.x * v.x + (double)v.y * v.y;
-    }
-    double part[1] = {block_sum(s, red)};
-    grid_reduce_last<1>(part, partials, &sc->counters[kCntInit], [&](const double *tot) {
-        sc->tau = tot[0];
-        sc->cg_done = !(tot[0] > sc->atol2);
-    });
-}
-
-// x += alpha d; r -= alpha A d; tau' = ||r||^2; beta_cg = tau'/tau; tau = tau'.
-// The step length is applied in FP64 (Alg. 2 keeps its scalars in double):
-// rounding alpha to FP32 alone moves the N=32 reconstruction by ~2.5e-3 NRMSE
-// against the FP64 solver, while FP32 vectors with FP64 scalars move it by
-// ~5e-5.  Each updated element is rounded to FP32 once.
-__global__ void cg_update_kernel(int npix, float2 *__restrict__ x, float2 *__restrict__ r,
-                                 const float2 *__restrict__ d, const float2 *__restrict__ ad, DevScalars *sc,
-                                 double *partials) {
-    if (sc->admm_done || sc->cg_done) return;
-    __shared__ double red[32];
-    const double alpha = sc->alpha;
-    double s = 0.0;
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < npix; n += gridDim.x * blockDim.x) {
-        const float2 dv = d[n], adv = ad[n];
-        float2 xv = x[n], rv = r[n];
-        xv.x = (float)fma(alpha, (double)dv.x, (double)xv.x);
-        xv.y = (float)fma(alpha, (double)dv.y, (double)xv.y);
-        rv.x = (float)fma(-alpha, (double)adv.x, (double)rv.x);
-        rv.y = (float)fma(-alpha, (double)adv.y, (double)rv.y);
-        x[n] = xv;
-        r[n] = rv;
-        s += (double)rv.x * rv.x + (double)rv.y * rv.y;
-    }
-    double part[1] = {block_sum(s, red)};
-    grid_reduce_last<1>(part, partials, &sc->counters[kCntTau], [&](const double *tot) {
-        sc->beta_cg = tot[0] / sc->tau;
-        sc->tau = tot[0];
-        sc->cg_done = !(tot[0] > sc->atol2);
-    });
-}
-
-// d = r + beta_cg d, with beta_cg applied in FP64 like alpha above
-__global__ void cg_direction_kernel(int npix, const float2 *__restrict__ r, float2 *__restrict__ d,
-                                    const DevScalars *sc) {
-    if (sc->admm_done || sc->cg_done) return;
-    const double bcg = sc->beta_cg;
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < npix; n += gridDim.x * blockDim.x) {
-        const float2 rv = r[n], dv = d[n];
-        d[n] = make_float2((float)fma(bcg, (double)dv.x, (double)rv.x), (float)fma(bcg, (double)dv.y, (double)rv.y));
-    }
-}
-
-// eta += Theta x - mu; alpha_admm = ||x - xprev||^2 / ||x||^2
-__global__ void admm_dual_kernel(int nx, int ny, const float2 *__restrict__ x, const float2 *__restrict__ xprev,
-                                 const float2 *__restrict__ mu, float2 *__restrict__ eta, DevScalars *sc,
-                                 double *partials, double *alpha_hist, int m) {
-    if (sc->admm_done) return;
-    __shared__ double red[32];
-    const int npix = nx * ny;
-    double num = 0.0, den = 0.0;
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < npix; n += gridDim.x * blockDim.x) {
-        const int i = n / ny, j = n % ny;
-        float2 gx, gy;
-        theta_at(x, i, j, nx, ny, gx, gy);
-        eta[n] = csub(cadd(eta[n], gx), mu[n]);
-        eta[npix + n] = csub(cadd(eta[npix + n], gy), mu[npix + n]);
-        const float2 xv = x[n], pv = xprev[n];
-        const double dx = (double)xv.x - pv.x, dy = (double)xv.y - pv.y;
-        num += dx * dx + dy * dy;
-        den += (double)xv.x * xv.x + (double)xv.y * xv.y;
-    }
-    double part[2];
-    part[0] = block_sum(num, red);
-    part[1] = block_sum(den, red);
-    grid_reduce_last<2>(part, partials, &sc->counters[kCntDual], [&](const double *tot) {
-        const double a = tot[0] / (tot[1] > 1e-300 ? tot[1] : 1e-300);
-        sc->admm_alpha = a;
-        if (alpha_hist) alpha_hist[m] = a;
-        sc->admm_done = !(a > sc->rtol2);
-    });
-}
-
-// f = ||y - d||^2 + lambda sum |Theta x|  (Eq. 3), with y = F x already in
-// yfx.  Recorded for every step that ran, including the one that met rtol.
-__global__ void objective_kernel(int nx, int ny, int nk, int nkc, const float2 *__restrict__ yfx, int yfx_ld,
-                                 const float2 *__restrict__ kspace, const float2 *__restrict__ x, float lambda,
-                                 DevScalars *sc, double *partials, double *obj_hist, int m) {
-    if (!sc->step_active) return;
-    __shared__ double red[32];
-    const int npix = nx * ny;
-    double fid = 0.0, l1 = 0.0;
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < nkc; n += gridDim.x * blockDim.x) {
-        const float2 r = csub(yfx[(size_t)(n / nk) * yfx_ld + n % nk], kspace[n]);
-        fid += (double)r.x * r.x + (double)r.y * r.y;
-    }
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < npix; n += gridDim.x * blockDim.x) {
-        float2 gx, gy;
-        theta_at(x, n / ny, n % ny, nx, ny, gx, gy);
-        l1 += sqrt((double)gx.x * gx.x + (double)gx.y * gx.y) + sqrt((double)gy.x * gy.x + (double)gy.y * gy.y);
-    }
-    double part[2];
-    part[0] = block_sum(fid, red);
-    part[1] = block_sum(l1, red);
-    grid_reduce_last<2>(part, partials, &sc->counters[kCntObj],
-                        [&](const double *tot) { obj_hist[m] = tot[0] + (double)lambda * tot[1]; });
-}
-
-__global__ void admm_reset_kernel(DevScalars *sc, double atol2, double rtol2) {
-    sc->tau = 0.0;
-    sc->alpha = 0.0;
-    sc->beta_cg = 0.0;
-    sc->admm_alpha = 1.0;
-    sc->atol2 = atol2;
-    sc->rtol2 = rtol2;
-    sc->cg_done = 0;
-    sc->admm_done = 0;
-    sc->step_active = 0;
-}
-
 int ew_blocks(int n) { return max(1, min(kEwMaxBlocks, ceil_div(n, kEwThreads))); }
 
 }  // namespace
@@ -337,58 +169,6 @@ cudaError_t launch_tv_adjoint(int nx, int ny, const float2 *g, float2 *x, cudaSt
 
 cudaError_t launch_shrink(int n, float t, const float2 *in, float2 *out, cudaStream_t s) {
     shrink_kernel<<<ceil_div(n, kEwThreads), kEwThreads, 0, s>>>(n, t, in, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_admm_mu(mri_plan *p, float thresh, cudaStream_t s) {
-    admm_mu_kernel<<<ceil_div(p->nx * p->ny, kEwThreads), kEwThreads, 0, s>>>(p->nx, p->ny, p->x, p->eta, p->mu,
-                                                                              p->xprev, thresh, p->scal);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_admm_rhs(mri_plan *p, float half_beta, cudaStream_t s) {
-    admm_rhs_kernel<<<ceil_div(p->nx * p->ny, kEwThreads), kEwThreads, 0, s>>>(p->nx, p->ny, p->fhd, p->mu, p->eta,
-                                                                               p->b, half_beta, p->scal);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_cg_init(mri_plan *p, cudaStream_t s) {
-    const int npix = p->nx * p->ny;
-    cg_init_kernel<<<ew_blocks(npix), kEwThreads, 0, s>>>(npix, p->b, p->ad, p->r, p->d, p->scal, p->partials);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_cg_update(mri_plan *p, cudaStream_t s) {
-    const int npix = p->nx * p->ny;
-    cg_update_kernel<<<ew_blocks(npix), kEwThreads, 0, s>>>(npix, p->x, p->r, p->d, p->ad, p->scal, p->partials);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_cg_direction(mri_plan *p, cudaStream_t s) {
-    const int npix = p->nx * p->ny;
-    cg_direction_kernel<<<ew_blocks(npix), kEwThreads, 0, s>>>(npix, p->r, p->d, p->scal);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_admm_dual(mri_plan *p, double *alpha_hist, int m, cudaStream_t s) {
-    const int npix = p->nx * p->ny;
-    admm_dual_kernel<<<ew_blocks(npix), kEwThreads, 0, s>>>(p->nx, p->ny, p->x, p->xprev, p->mu, p->eta, p->scal,
-                                                            p->partials, alpha_hist, m);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_objective(mri_plan *p, const float2 *kspace, float lambda, double *obj_hist, int m,
-                             cudaStream_t s) {
-    const int npix = p->nx * p->ny;
-    const int nkc = p->nk * p->nc;
-    objective_kernel<<<ew_blocks(max(npix, nkc)), kEwThreads, 0, s>>>(p->nx, p->ny, p->nk, nkc, p->y, p->nk_pad,
-                                                                      kspace, p->x, lambda, p->scal, p->partials,
-                                                                      obj_hist, m);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_admm_reset(mri_plan *p, double atol, double rtol, cudaStream_t s) {
-    admm_reset_kernel<<<1, 1, 0, s>>>(p->scal, atol * atol, rtol * rtol);
     return cudaGetLastError();
 }
 
