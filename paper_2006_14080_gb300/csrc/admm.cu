@@ -13,7 +13,8 @@
 // per reconstruction.
 //
 // One CG step of Alg. 2 after the two products is a single cooperative
-// kernel: (1) the fixed-order sum of the partial images and the coil
+// kernel (or, for reconstructions that share the GPU with others, the same
+// arithmetic as two ordinary kernels split at the barrier): (1) the fixed-order sum of the partial images and the coil
 // combination give A d (with the (beta/2) Theta^H Theta d term), and the
 // dot products Re<d, A d>, Re<r, A d> and ||A d||^2; one grid barrier;
 // (2) alpha = tau / Re<d, A d>, tau' = ||r - alpha A d||^2 from the expanded
@@ -146,9 +147,8 @@ struct Partials {
     int stage_elems;      // complex values per stage: cs * chunk, at least kMinStageElems
 };
 
-// A stage holds at least 1024 complex values (16 KB over the two stages):
-// the CG step reuses the ring for its per-block partial triples (3 doubles
-// for each of at most 2 x 152 blocks).
+// A stage holds at least 1024 complex values: the CG step reuses the ring
+// (2 x 1024 doubles) to stage its per-item partial triples.
 constexpr int kMinStageElems = 1024;
 
 constexpr int kRingStages = 2;
@@ -194,11 +194,12 @@ __device__ __forceinline__ void issue_unit(const Partials &P, const Ring &R, int
 // row's running value in increasing coil order; the rows are then added in
 // increasing order.  For each item, epi(item, j, ig, i, v) runs in thread
 // rows 0 and 1 (pixel i = 64 ig + 2 tx + ty, v its value; i may lie past
-// the image).  Returns false if a stage wait ran out (kStatusTimeout is
-// recorded).  All threads of the block must call it.
-template <typename Epi>
+// the image), then done(item) in every thread.  Returns false if a stage
+// wait ran out (kStatusTimeout is recorded).  All threads of the block must
+// call it.
+template <typename Epi, typename Done>
 __device__ __forceinline__ bool staged_items(const Partials &P, const Ring &R, int n_items, int *status,
-                                             float4 (*grp)[kRedThreadsX], Epi epi) {
+                                             float4 (*grp)[kRedThreadsX], Epi epi, Done done) {
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int my_items = n_items > (int)blockIdx.x ? (n_items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int units = my_items * P.n_groups;
@@ -244,6 +245,7 @@ __device__ __forceinline__ bool staged_items(const Partials &P, const Ring &R, i
                 epi(item, item / P.n_ig, item % P.n_ig, (item % P.n_ig) * 64 + 2 * tx + ty, v);
             }
             __syncthreads();  // grp is free again
+            done(item);       // all threads
         }
     }
     if (!ok && flat_tid() == 0) {
@@ -325,23 +327,29 @@ __device__ __forceinline__ void rows01_sum3(double (&v)[3], double (*scratch)[2]
         for (int q = 0; q < 3; ++q) v[q] = scratch[q][0] + scratch[q][1];
 }
 
-// The per-block partial triples [0, n) summed in a fixed order: the block
-// stages them in shared memory with one load per thread (no chain of
-// dependent global loads), then warp 0 adds them, lane l taking blocks
-// l, l + 32, ... in order, and the lanes are combined.  Valid in flat thread
-// 0; stage holds at least 3 n doubles.
-__device__ __forceinline__ void sum_partials3(const double *partials, int n, double *stage, double (&t)[3]) {
-    for (int q = flat_tid(); q < 3 * n; q += blockDim.x * blockDim.y) stage[q] = __ldcg(&partials[q]);
-    __syncthreads();
+// The per-item partial triples [0, n) summed in a fixed order that does not
+// depend on the grid: warp 0 adds them, lane l taking items l, l + 32, ...
+// in increasing order, then the lanes are combined.  They are staged through
+// shared memory (cap doubles at a time, one load per thread, no chain of
+// dependent global loads).  Valid in flat thread 0.
+__device__ __forceinline__ void sum_partials3(const double *partials, int n, double *stage, int cap,
+                                              double (&t)[3]) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) t[q] = 0.0;
-    if (flat_tid() < 32) {
-        for (int b = flat_tid(); b < n; b += 32)
+    const int per = cap / 96 * 32;  // items per chunk, a multiple of 32
+    for (int b0 = 0; b0 < n; b0 += per) {
+        const int m = min(per, n - b0);
+        __syncthreads();
+        for (int q = flat_tid(); q < 3 * m; q += blockDim.x * blockDim.y) stage[q] = __ldcg(&partials[3 * b0 + q]);
+        __syncthreads();
+        if (flat_tid() < 32)
+            for (int b = flat_tid(); b < m; b += 32)
 #pragma unroll
-            for (int q = 0; q < 3; ++q) t[q] += stage[3 * b + q];
+                for (int q = 0; q < 3; ++q) t[q] += stage[3 * b + q];
+    }
+    if (flat_tid() < 32)
 #pragma unroll
         for (int q = 0; q < 3; ++q) t[q] = warp_sum(t[q]);
-    }
 }
 
 struct CgArgs {
@@ -357,60 +365,34 @@ struct CgArgs {
     int n_items;       // n_ig * ny
 };
 
-template <int kMode>
-__global__ void __launch_bounds__(kRedThreads, 2) cg_step_kernel(const CgArgs A) {
-    if (should_skip(A.sc, kSkipCg)) return;
-    extern __shared__ __align__(128) uint8_t dyn_smem[];
-    __shared__ float4 grp[kRedGroups][kRedThreadsX];
-    __shared__ double red3[3][2];
-    __shared__ double scal_s[3];
-    __shared__ int abort_s;
-    const int nx = A.P.nx, ny = A.P.ny;
-    const size_t npix = (size_t)nx * ny;
-    const double tau = A.sc->tau;
-    const Ring R = make_ring(A.P, dyn_smem, &abort_s);
-    // (1) A d, and Re<d, A d>, Re<r, A d>, ||A d||^2
-    double s_dad = 0.0, s_rad = 0.0, s_aa = 0.0;
-    staged_items(A.P, R, A.n_items, &A.sc->status, grp, [&](int, int j, int, int i, float2 v) {
-        if (i >= nx) return;
-        const float2 tt = theta_h_thetaT(A.d, i, j, nx, ny);
-        v.x = fmaf(A.half_beta, tt.x, v.x);
-        v.y = fmaf(A.half_beta, tt.y, v.y);
-        const size_t n = (size_t)j * nx + i;
-        A.ad[n] = v;
-        const float2 dv = A.d[n], rv = A.r[n];
-        s_dad += (double)dv.x * (double)v.x + (double)dv.y * (double)v.y;
-        s_rad += (double)rv.x * (double)v.x + (double)rv.y * (double)v.y;
-        s_aa += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
-    });
-    double v3[3] = {s_dad, s_rad, s_aa};
-    rows01_sum3(v3, red3);
-    if (flat_tid() == 0)
-        for (int q = 0; q < 3; ++q) A.partials[3 * blockIdx.x + q] = v3[q];
-    if (!grid_barrier(A.bar, &A.sc->status)) return;
-    // (2) every block sums the partials in block order: alpha, then
-    // tau' = ||r - alpha A d||^2 = tau - 2 alpha Re<r, A d> + alpha^2 ||A d||^2
-    // (the square expanded, so that one grid-wide reduction serves alpha and
-    // beta), beta = tau' / tau
+// alpha = tau / Re<d, A d>, tau' = ||r - alpha A d||^2 = tau - 2 alpha
+// Re<r, A d> + alpha^2 ||A d||^2 (the square expanded, so that one
+// grid-wide reduction serves alpha and beta) and beta = tau' / tau, from the
+// per-item partial triples; out[0..2] = alpha, tau', beta in every thread.
+__device__ __forceinline__ void cg_scalars(const double *partials, int n_items, double *stage, double tau,
+                                           double *out) {
     double t3[3];
-    // the ring is free now: it holds the partial triples (3 gridDim.x <= 2
-    // kMinStageElems doubles: the grid is at most two blocks per SM)
-    sum_partials3(A.partials, gridDim.x, reinterpret_cast<double *>(R.buf), t3);
+    sum_partials3(partials, n_items, stage, 2 * kMinStageElems, t3);
     if (flat_tid() == 0) {
         const double alpha = tau / t3[0];
         const double tau_next = tau - 2.0 * alpha * t3[1] + alpha * alpha * t3[2];
-        scal_s[0] = alpha;
-        scal_s[1] = tau_next;
-        scal_s[2] = tau_next / tau;
+        out[0] = alpha;
+        out[1] = tau_next;
+        out[2] = tau_next / tau;
     }
     __syncthreads();
-    const double alpha = scal_s[0], tau_next = scal_s[1], beta = scal_s[2];
+}
+
+// The updates of a CG step over the grid-stride loop of (coil, pixel) pairs
+// starting at gtid: r' = r - alpha A d and d' = r' + beta d at each pair's
+// pixel (the same values for every coil) and the operand entry S_c d';
+// coil 0 stores x += alpha d, r' and d' (r' and d' into the other buffers:
+// r and d are still being read).
+template <int kMode>
+__device__ __forceinline__ void cg_updates(const CgArgs &A, double alpha, double beta, size_t gtid, size_t gstride) {
+    const int nx = A.P.nx, ny = A.P.ny;
+    const size_t npix = (size_t)nx * ny;
     const Split sa = split_scalar(alpha), sna = split_scalar(-alpha), sb = split_scalar(beta);
-    // (3) one (coil, pixel) pair per thread: r' = r - alpha A d and
-    // d' = r' + beta d at its pixel (the same values for every coil), and
-    // the operand entry S_c d'; coil 0 stores x += alpha d, r' and d' (r'
-    // and d' into the other buffers: r and d are still being read)
-    const size_t gtid = (size_t)blockIdx.x * kRedThreads + flat_tid(), gstride = (size_t)gridDim.x * kRedThreads;
     const size_t total = npix * A.P.nc;
     for (size_t e0 = gtid; e0 < total; e0 += 2 * gstride) {
         // two pairs e0 and e0 + gstride per pass, loads of both issued first
@@ -441,11 +423,117 @@ __global__ void __launch_bounds__(kRedThreads, 2) cg_step_kernel(const CgArgs A)
             put_operand_one<kMode>(A.op, A.P.mapsT, A.P.n_ig * 64, ny, e0 + h * gstride, c[h], n[h], nx, nd);
         }
     }
+}
+
+// Step (1) of a CG step over the block's items: A d (written to ad) and the
+// per-item partial triples Re<d, A d>, Re<r, A d>, ||A d||^2 (each item's 64
+// pixels summed in thread order), so that the sums that follow do not
+// depend on how items map to blocks.
+template <int kMode>
+__device__ __forceinline__ void cg_reduce_items(const CgArgs &A, const Ring &R, float4 (*grp)[kRedThreadsX],
+                                                double (*red3)[2]) {
+    const int nx = A.P.nx, ny = A.P.ny;
+    double v3[3] = {0.0, 0.0, 0.0};
+    staged_items(
+        A.P, R, A.n_items, &A.sc->status, grp,
+        [&](int, int j, int, int i, float2 v) {
+            if (i >= nx) return;
+            const float2 tt = theta_h_thetaT(A.d, i, j, nx, ny);
+            v.x = fmaf(A.half_beta, tt.x, v.x);
+            v.y = fmaf(A.half_beta, tt.y, v.y);
+            const size_t n = (size_t)j * nx + i;
+            A.ad[n] = v;
+            const float2 dv = A.d[n], rv = A.r[n];
+            v3[0] = (double)dv.x * (double)v.x + (double)dv.y * (double)v.y;
+            v3[1] = (double)rv.x * (double)v.x + (double)rv.y * (double)v.y;
+            v3[2] = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+        },
+        [&](int item) {
+            rows01_sum3(v3, red3);
+            if (flat_tid() == 0)
+                for (int q = 0; q < 3; ++q) A.partials[3 * item + q] = v3[q];
+            v3[0] = v3[1] = v3[2] = 0.0;
+        });
+}
+
+// Whether this block is the last of the grid to arrive (counter reset by it).
+__device__ __forceinline__ bool last_block_arrives(unsigned *counter) {
+    __shared__ int last_s;
+    __syncthreads();
+    if (flat_tid() == 0) {
+        __threadfence();
+        const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+        const unsigned t = atomicAdd(counter, 1u);
+        last_s = t == nblocks - 1;
+        if (last_s) *counter = 0u;
+        __threadfence();
+    }
+    __syncthreads();
+    return last_s != 0;
+}
+
+// A whole CG step as one cooperative kernel: (1) over the items, one grid
+// barrier, then every block forms the scalars and (3) the updates.
+template <int kMode>
+__global__ void __launch_bounds__(kRedThreads, 2) cg_step_kernel(const CgArgs A) {
+    if (should_skip(A.sc, kSkipCg)) return;
+    extern __shared__ __align__(128) uint8_t dyn_smem[];
+    __shared__ float4 grp[kRedGroups][kRedThreadsX];
+    __shared__ double red3[3][2];
+    __shared__ double scal_s[3];
+    __shared__ int abort_s;
+    const double tau = A.sc->tau;
+    const Ring R = make_ring(A.P, dyn_smem, &abort_s);
+    cg_reduce_items<kMode>(A, R, grp, red3);
+    if (!grid_barrier(A.bar, &A.sc->status)) return;
+    // every block forms the same scalars (the ring now stages the partials)
+    cg_scalars(A.partials, A.n_items, reinterpret_cast<double *>(R.buf), tau, scal_s);
+    const double alpha = scal_s[0], tau_next = scal_s[1], beta = scal_s[2];
+    cg_updates<kMode>(A, alpha, beta, (size_t)blockIdx.x * kRedThreads + flat_tid(), (size_t)gridDim.x * kRedThreads);
     if (blockIdx.x == 0 && flat_tid() == 0) {
         A.sc->alpha = alpha;
         A.sc->beta_cg = beta;
         A.sc->tau = tau_next;
         A.sc->cg_done = !(tau_next > A.sc->atol2);
+    }
+}
+
+// The same CG step as two ordinary kernels.  The reduction: one item per
+// block; the last block to finish forms the scalars from the same partials
+// in the same order and hands them to the update kernel.
+template <int kMode>
+__global__ void __launch_bounds__(kRedThreads, 2) cg_reduce_kernel(const CgArgs A) {
+    if (should_skip(A.sc, kSkipCg)) return;
+    extern __shared__ __align__(128) uint8_t dyn_smem[];
+    __shared__ float4 grp[kRedGroups][kRedThreadsX];
+    __shared__ double red3[3][2];
+    __shared__ double scal_s[3];
+    __shared__ int abort_s;
+    const double tau = A.sc->tau;
+    const Ring R = make_ring(A.P, dyn_smem, &abort_s);
+    cg_reduce_items<kMode>(A, R, grp, red3);
+    if (!last_block_arrives(&A.sc->counters[kCntDot])) return;
+    cg_scalars(A.partials, A.n_items, reinterpret_cast<double *>(R.buf), tau, scal_s);
+    if (flat_tid() == 0) {
+        A.sc->alpha = scal_s[0];
+        A.sc->tau_next = scal_s[1];
+        A.sc->beta_cg = scal_s[2];
+        A.sc->step_pending = 1;
+    }
+}
+
+// The updates of the two-kernel CG step, one (coil, pixel) pair per thread.
+template <int kMode>
+__global__ void cg_update_kernel(const CgArgs A) {
+    if (A.sc->admm_done || !A.sc->step_pending) return;
+    const double alpha = A.sc->alpha, beta = A.sc->beta_cg;
+    cg_updates<kMode>(A, alpha, beta, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
+    if (!last_block_arrives(&A.sc->counters[kCntTau])) return;
+    if (threadIdx.x == 0) {
+        const double tau_next = A.sc->tau_next;
+        A.sc->tau = tau_next;
+        A.sc->cg_done = !(tau_next > A.sc->atol2);
+        A.sc->step_pending = 0;
     }
 }
 
@@ -476,7 +564,7 @@ __global__ void __launch_bounds__(kRedThreads, 2)
         d[n] = rv;
         rs[i - ig * 64] = rv;
         s = (double)rv.x * rv.x + (double)rv.y * rv.y;
-    });
+    }, [](int) {});
     // the operand of d = r at the block's pixels, one (coil, pixel) pair per thread
     const int ig = blockIdx.x % P.n_ig, j = blockIdx.x / P.n_ig;
     const int npx = min(64, P.nx - ig * 64);
@@ -500,9 +588,12 @@ __global__ void __launch_bounds__(kRedThreads, 2) fhd_kernel(const Partials P, f
     __shared__ float4 grp[kRedGroups][kRedThreadsX];
     __shared__ int abort_s;
     const Ring R = make_ring(P, dyn_smem, &abort_s);
-    staged_items(P, R, gridDim.x, status, grp, [&](int, int j, int, int i, float2 v) {
-        if (i < P.nx) out[(size_t)j * P.nx + i] = v;
-    });
+    staged_items(
+        P, R, gridDim.x, status, grp,
+        [&](int, int j, int, int i, float2 v) {
+            if (i < P.nx) out[(size_t)j * P.nx + i] = v;
+        },
+        [](int) {});
 }
 
 // Opens an ADMM step (Eq. 8 and 12): mu = S_t(Theta x + eta), b = F^H d +
@@ -640,6 +731,8 @@ __global__ void admm_reset_kernel(DevScalars *sc, unsigned *bar, double atol2, d
     sc->cg_done = 0;
     sc->admm_done = 0;
     sc->step_active = 0;
+    sc->step_pending = 0;
+    sc->tau_next = 0.0;
     bar[0] = 0u;  // a barrier that ran out of time may have left arrivals counted
 }
 
@@ -689,7 +782,7 @@ int operand_mode(const mri_plan *p) {
 }
 
 template <int kMode>
-cudaError_t launch_cg_step_t(mri_plan *p, float half_beta, int it, cudaStream_t s) {
+CgArgs cg_args(mri_plan *p, float half_beta, int it) {
     CgArgs A;
     A.P = partials_of(p);
     A.x = p->x;
@@ -705,6 +798,12 @@ cudaError_t launch_cg_step_t(mri_plan *p, float half_beta, int it, cudaStream_t 
     A.partials = p->partials;
     A.bar = p->grid_bar;
     A.n_items = A.P.n_ig * p->ny;
+    return A;
+}
+
+template <int kMode>
+cudaError_t launch_cg_step_t(mri_plan *p, float half_beta, int it, cudaStream_t s) {
+    const CgArgs A = cg_args<kMode>(p, half_beta, it);
     const size_t smem = ring_bytes(A.P);
     cudaError_t e = allow_smem(cg_step_kernel<kMode>, smem);
     if (e != cudaSuccess) return e;
@@ -719,6 +818,19 @@ cudaError_t launch_cg_step_t(mri_plan *p, float half_beta, int it, cudaStream_t 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, cg_step_kernel<kMode>, A);
+}
+
+template <int kMode>
+cudaError_t launch_cg_step_split_t(mri_plan *p, float half_beta, int it, cudaStream_t s) {
+    const CgArgs A = cg_args<kMode>(p, half_beta, it);
+    const size_t smem = ring_bytes(A.P);
+    cudaError_t e = allow_smem(cg_reduce_kernel<kMode>, smem);
+    if (e != cudaSuccess) return e;
+    cg_reduce_kernel<kMode><<<A.n_items, dim3(kRedThreadsX, kRedGroups), smem, s>>>(A);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cg_update_kernel<kMode><<<ew_blocks((size_t)p->nx * p->ny * p->nc), kEwThreads, 0, s>>>(A);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -737,8 +849,7 @@ int cg_step_grid(const mri_plan *p) {
     const long items = (long)(p->nx_pad / 64) * p->ny;
     const long pix_blocks = ((long)p->nx * p->ny + kRedThreads - 1) / kRedThreads;
     const long want = std::max(items, pix_blocks);
-    const long cap = std::min<long>((long)per_sm * p->num_sms, 2L * kMinStageElems / 3);  // partial triples fit the ring
-    return (int)std::max(1L, std::min<long>(cap, want));
+    return (int)std::max(1L, std::min<long>((long)per_sm * p->num_sms, want));
 }
 
 cudaError_t launch_transpose(const float2 *src, float2 *dst, int rows, int cols, int planes, cudaStream_t s,
@@ -812,6 +923,17 @@ cudaError_t launch_cg_step(mri_plan *p, float half_beta, int it, cudaStream_t s)
         return launch_cg_step_t<kOpTf32>(p, half_beta, it, s);
     default:
         return launch_cg_step_t<kOpFp32>(p, half_beta, it, s);
+    }
+}
+
+cudaError_t launch_cg_step_split(mri_plan *p, float half_beta, int it, cudaStream_t s) {
+    switch (operand_mode(p)) {
+    case kOpBf16x3:
+        return launch_cg_step_split_t<kOpBf16x3>(p, half_beta, it, s);
+    case kOpTf32:
+        return launch_cg_step_split_t<kOpTf32>(p, half_beta, it, s);
+    default:
+        return launch_cg_step_split_t<kOpFp32>(p, half_beta, it, s);
     }
 }
 

@@ -502,7 +502,7 @@ MRI_API int mri_soft_threshold(int n, float t, const mri_c64 *in, mri_c64 *out, 
 // one cooperative kernel that finishes the adjoint and takes the CG step.
 int mri::enqueue_admm(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in, const mri_admm_params *prm,
                       mri_c64 *image_out, double *objective_hist, double *alpha_hist, cudaStream_t s,
-                      const AdmmWarm &warm) {
+                      const AdmmWarm &warm, bool coop) {
     const float2 *kspace = (const float2 *)kspace_in;
     const float2 *maps = (const float2 *)maps_in;
     const size_t npix = (size_t)p->nx * p->ny;
@@ -544,7 +544,13 @@ int mri::enqueue_admm(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps
         for (int it = 0; it < prm->cg_iters; ++it) {
             STEP(solver_forward(p, kSkipCg, s));                // F d (operand written by the kernel before)
             STEP(op_adjoint_partials(p, p->y, kSkipCg, s));     // F^H F d, partial images
-            STEP(solver_cg_step(p, half_beta, it, s));          // A d, alpha, x, r, beta, d, operand of d
+            // A d, alpha, x, r, beta, d, operand of d
+            if (coop) {
+                STEP(solver_cg_step(p, half_beta, it, s));
+            } else {
+                STEP(launch_cg_step_split(p, half_beta, it, s));
+                p->launches += 2;
+            }
         }
         const bool obj = objective_hist != nullptr;
         KERNEL(launch_dual(p, obj, alpha_hist, m, s));  // Eq. 8 (dual), Alg. 4 relative change

@@ -99,8 +99,10 @@ MRI_API int mri_batch_reconstruct(mri_batch *b, int n, const mri_request *reqs, 
             const long long l0 = r.plan->launches;
             e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) break;
+            // the items run concurrently: CG steps as ordinary kernels (a
+            // cooperative grid would wait for the whole GPU), same results
             const int rc = enqueue_admm(r.plan, r.kspace, r.coil_maps, &r.params, r.image_out, nullptr, nullptr,
-                                        b->capture);
+                                        b->capture, AdmmWarm(), false);
             cudaGraph_t child = nullptr;
             e = cudaStreamEndCapture(b->capture, &child);
             if (rc != MRI_OK || e != cudaSuccess) {

@@ -31,6 +31,8 @@ struct DevScalars {
     int admm_done;      // ADMM has met its tolerance
     int status;         // 0, or a device-side failure code (see kStatus*)
     int step_active;    // the current ADMM step runs (ADMM had not stopped when it began)
+    double tau_next;    // two-kernel CG step: ||r'||^2, handed from the reduction to the update
+    int step_pending;   // two-kernel CG step: the reduction ran and its update is due
     unsigned counters[8];  // grid-reduction tickets, one per reduction site
 };
 
@@ -192,9 +194,13 @@ struct AdmmWarm {
     mri_c64 *eta_out = nullptr;
 };
 // Enqueue one whole reconstruction (Alg. 4 with Alg. 2) on s; MRI_* status.
+// coop: each CG step as one cooperative kernel (a single reconstruction on
+// the stream); else as two ordinary kernels with the same arithmetic and
+// results, for reconstructions that run concurrently with others (batches,
+// the server), where a cooperative grid would wait for the whole GPU.
 int enqueue_admm(mri_plan *p, const mri_c64 *kspace, const mri_c64 *maps, const mri_admm_params *prm,
                  mri_c64 *image_out, double *objective_hist, double *alpha_hist, cudaStream_t s,
-                 const AdmmWarm &warm = AdmmWarm());
+                 const AdmmWarm &warm = AdmmWarm(), bool coop = true);
 }  // namespace mri
 
 // Record the timing events (when set) immediately around a product kernel.
@@ -260,6 +266,8 @@ cudaError_t launch_cg_init(mri_plan *p, float half_beta, cudaStream_t s);
 // cooperative; step `it` of a CG solve reads the residual and direction
 // from r, d (it even) or r2, d2 (odd) and leaves the next ones in the others
 cudaError_t launch_cg_step(mri_plan *p, float half_beta, int it, cudaStream_t s);
+// the same CG step as two ordinary kernels (reduction, then the updates)
+cudaError_t launch_cg_step_split(mri_plan *p, float half_beta, int it, cudaStream_t s);
 cudaError_t launch_dual(mri_plan *p, bool operand, double *alpha_hist, int m, cudaStream_t s);
 cudaError_t launch_objective(mri_plan *p, const float2 *kspace, float lambda, double *obj_hist, int m,
                              cudaStream_t s);

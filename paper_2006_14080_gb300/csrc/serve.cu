@@ -157,8 +157,13 @@ int start_job(mri_server *s, Job *j) {
         if (rc != MRI_OK) return rc;
         pe->traj_hash = j->traj_hash;
     }
-    int rc = mri_admm_reconstruct(pe->plan, (const mri_c64 *)j->d_k, (const mri_c64 *)j->d_maps, &r.params,
-                                  (mri_c64 *)j->d_img, nullptr, nullptr, st);
+    // requests run concurrently: CG steps as ordinary kernels (a cooperative
+    // grid would wait for the whole GPU), the same results as alone
+    int rc = mri::check_admm_args(pe->plan, (const mri_c64 *)j->d_k, (const mri_c64 *)j->d_maps, &r.params,
+                                  (const mri_c64 *)j->d_img);
+    if (rc == MRI_OK)
+        rc = mri::enqueue_admm(pe->plan, (const mri_c64 *)j->d_k, (const mri_c64 *)j->d_maps, &r.params,
+                               (mri_c64 *)j->d_img, nullptr, nullptr, st, mri::AdmmWarm(), false);
     if (rc != MRI_OK) return rc;
     e = cudaMemcpyAsync(j->h_img, j->d_img, j->img_bytes, cudaMemcpyDeviceToHost, st);
     // the plan's deferred status word (bounded device waits) travels with the image
