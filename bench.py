@@ -44,15 +44,15 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # product kernels on this workload, from one ncu capture each (the summaries
-# under profiles/ give the command), keyed by a hash of the kernel sources as
-# captured: a changed kernel reports traffic null until it is captured again.
+# under profiles/ give the command), keyed by a hash of the product kernels'
+# sources as captured: a changed kernel reports traffic null until it is
+# captured again.
 NCU_TRAFFIC = {
-    ("adj_tc_kernel", "n128_c12_s64x256"): (41.93e6, "eb706c3214104728", "profiles/adj_tc_kernel_n128.md"),
-    ("fwd_tc_kernel", "n128_c12_s64x256"): (52.78e6, "eb706c3214104728", "profiles/fwd_tc_kernel_n128.md"),
-    ("adj_tc_kernel", "n256_c32_s128x512"): (1303.0e6, "eb706c3214104728", "profiles/adj_tc_kernel_n256.md"),
-    ("fwd_tc_kernel", "n256_c32_s128x512"): (438.9e6, "eb706c3214104728", "profiles/fwd_tc_kernel_n256.md"),
+    ("adj_tc_kernel", "n128_c12_s64x256"): (40.57e6, "c4f865303c5ac601", "profiles/adj_tc_kernel_n128.md"),
+    ("fwd_tc_kernel", "n128_c12_s64x256"): (52.05e6, "c4f865303c5ac601", "profiles/fwd_tc_kernel_n128.md"),
+    ("adj_tc_kernel", "n256_c32_s128x512"): (1302.56e6, "c4f865303c5ac601", "profiles/adj_tc_kernel_n256.md"),
 }
-TC_SOURCES = ("nudft_tc.cu", "tc_ptx.cuh", "internal.h", "common.cuh")
+TC_SOURCES = ("nudft_tc.cu", "tc_ptx.cuh")
 
 
 def tc_source_hash() -> str:
