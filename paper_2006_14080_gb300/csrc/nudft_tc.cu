@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             if (g >= P.num_units) break;
             const int a = lt & 1;
             const uint32_t ap = (lt >> 1) & 1;
-            if (!mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs))) break;
             fence_after_sync();
             const int m_blk = g / P.n_tiles, n_blk = g % P.n_tiles;
             if (part == 0) {
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             }
             bool ok = true;
             for (int jc = 0; jc < n_jc; ++jc) {
-                if (!mbar_wait(yfull0 + 8 * yr.stage, yr.phase, abort_flag, kWaitLimitNs)) {
+                if (!__all_sync(0xffffffffu, mbar_wait(yfull0 + 8 * yr.stage, yr.phase, abort_flag, kWaitLimitNs))) {
                     ok = false;
                     break;
                 }
@@ -451,6 +451,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     fence_before_sync();
     __syncthreads();
     if (warp == 1) {
+        __syncwarp();  // lane 0 ran the issue loop alone; dealloc is .sync.aligned
         fence_after_sync();
         tmem_dealloc(tmem_base, P.tmem_cols);
     }
@@ -542,13 +543,19 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         Ring rr, rs;
         uint32_t issued_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int issued_mask = 0;
-        for (int u = blockIdx.x; u < P.num_units && !*abort_flag; u += gridDim.x) {
+        // every branch below is warp-uniform: the waits' outcomes are agreed
+        // on with __all_sync and the warp reconverges after the one-thread
+        // TMA issue, because tcgen05.st / wait::st are .sync.aligned and a
+        // warp that reached them diverged stored part of its lanes late
+        for (int u = blockIdx.x; u < P.num_units; u += gridDim.x) {
+            if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
             const int p = u / P.m_tiles;
             const int kb0 = p * P.kb_per_split, kb1 = min(P.num_kb, kb0 + P.kb_per_split);
             bool ok = true;
             for (int kb = kb0; kb < kb1; ++kb) {
-                if (!mbar_wait(rfull0 + 8 * rr.stage, rr.phase, abort_flag, kWaitLimitNs) ||
-                    !mbar_wait(empty0 + 8 * rs.stage, rs.phase ^ 1, abort_flag, kWaitLimitNs)) {
+                const bool waited = mbar_wait(rfull0 + 8 * rr.stage, rr.phase, abort_flag, kWaitLimitNs) &&
+                                    mbar_wait(empty0 + 8 * rs.stage, rs.phase ^ 1, abort_flag, kWaitLimitNs);
+                if (!__all_sync(0xffffffffu, waited)) {
                     ok = false;
                     break;
                 }
@@ -563,6 +570,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
                     issued_phase[rs.stage] = rs.phase;
                     issued_mask |= 1 << rs.stage;
                 }
+                __syncwarp();
                 // staged A_x^H half-row (128-byte swizzled, sixteen samples) and
                 // y_c chunk: this thread's samples are chunks chunk0 + kCpt o + c
                 const uint8_t *arow = raw + (size_t)rr.stage * kRawB + (kPx128 ? half * (kRawQ0 / 2) + (ii >> 4) * 128
@@ -782,7 +790,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         for (int u = blockIdx.x; u < P.num_units; u += gridDim.x, ++lt) {
             const int a = lt % NA;
             const uint32_t ap = (lt / NA) & 1;
-            if (!mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs)) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * a, ap, abort_flag, kWaitLimitNs))) break;
             fence_after_sync();
             const int p = u / P.m_tiles, m = u % P.m_tiles;
             const int c = m % P.nc, ib = m / P.nc;
@@ -830,6 +838,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
     fence_before_sync();
     __syncthreads();
     if (warp == kAdjMmaWarp) {
+        __syncwarp();  // lane 0 ran the issue loop alone; dealloc is .sync.aligned
         fence_after_sync();
         tmem_dealloc(tmem_base, P.tmem_cols);
     }

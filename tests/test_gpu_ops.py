@@ -183,6 +183,34 @@ def test_tile_configurations_change_schedule_not_results(mr):
     assert _rel(ref_a, oracle.adjoint(traj, y, maps)) <= OP_TOL["bf16x3"]
 
 
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32", "fp32"])
+def test_repeated_calls_and_plans_are_bit_identical(mr, precision):
+    # every operator sums in a fixed order, so repeating a call, or making it
+    # on a second plan of the same shape, must give the same bits.  The
+    # 128 x 128 image with 12 coils and 16,384 samples takes the pixel-row
+    # adjoint with a dozen or more K splits per coil: the shape on which a
+    # producer warp that reached its .sync.aligned TMEM stores diverged left
+    # some lanes' operand rows late and changed the TF32 adjoint from call
+    # to call (up to 3.6e-3 relative, rows 0-31 only)
+    nx, ny, nc = 128, 128, 12
+    maps, traj, x, y = _case(nx, ny, nc, 64, 256, seed=41)
+    dm, dx, dy, dt = _dev(maps), _dev(x), _dev(y), _dev(traj, torch.float32)
+    runs = []
+    for _ in range(2):
+        with mr.Plan(nx, ny, nc, dt, precision) as plan:
+            a0 = mr.nudft_adjoint(plan, dy, dm).cpu().numpy()
+            for _ in range(7):
+                assert np.array_equal(mr.nudft_adjoint(plan, dy, dm).cpu().numpy(), a0)
+            f0 = mr.nudft_forward(plan, dx, dm).cpu().numpy()
+            n0 = mr.normal_op(plan, dx, dm, beta=1.0).cpu().numpy()
+            assert np.array_equal(mr.normal_op(plan, dx, dm, beta=1.0).cpu().numpy(), n0)
+            plan.sync_status()
+        runs.append((a0, f0, n0))
+    for u, v in zip(runs[0], runs[1]):
+        assert np.array_equal(u, v)
+    assert _rel(runs[0][0], oracle.adjoint(traj, y, maps)) <= OP_TOL[precision]
+
+
 def test_invalid_arguments_are_rejected(mr):
     import ctypes
     lib = mr.load()
