@@ -240,13 +240,21 @@ MRI_API long long mri_batch_launch_count(const mri_batch *batch);
  * concurrently (continuous batching).
  *
  * A server owns a scheduler thread, `max_inflight` CUDA streams, a device
- * memory pool for request buffers and a cache of plans keyed by shape and
- * trajectory contents.  The scheduler starts the oldest waiting request
- * (first in, first out) as soon as a stream is free and its device bytes --
- * the plan's (mri_plan_estimate_bytes, unless an idle cached plan of the
- * same key exists) plus its k-space, maps, trajectory and image buffers --
- * fit under `hbm_budget_bytes` together with everything resident; idle
- * cached plans are evicted least-recently-used to make room.  A request whose bytes exceed the whole budget
+ * memory pool and a cache of entries: an entry is a plan for one shape and
+ * trajectory (its DFT factors) with fixed device buffers for that shape's
+ * k-space, coil maps and image, which stay resident between requests.  A
+ * request whose trajectory equals an idle entry's (byte for byte) reuses
+ * the entry's factors; if its coil maps also equal the entry's, they are
+ * not uploaded again.  From an entry's second request on, the
+ * reconstruction runs as a CUDA graph captured once over the entry's
+ * buffers and then replayed.  The scheduler starts the oldest waiting
+ * request (first in, first out) as soon as a stream is free and its device
+ * bytes -- a new entry's (mri_plan_estimate_bytes plus the three buffers)
+ * and the trajectory upload, or nothing beyond the trajectory upload for a
+ * cached entry -- fit under `hbm_budget_bytes` together with everything
+ * resident; idle entries are evicted least-recently-used to make room, and
+ * when nothing else fits an idle entry of the request's shape is given the
+ * new trajectory in place.  A request whose bytes exceed the whole budget
  * fails with MRI_ERR_NOMEM; one whose shape the precision does not support
  * fails with MRI_ERR_NOMEM too (estimate 0).  Every request runs Alg. 4
  * with its own plan and buffers, so its image is bit-identical to the one
@@ -292,6 +300,14 @@ MRI_API int mri_server_wait(mri_server *server, uint64_t ticket, mri_c64 *image,
  * now and at most so far by cached plans and in-flight requests. */
 MRI_API int mri_server_stats(mri_server *server, double *p50_ms, double *p99_ms, uint64_t *completed,
                              uint64_t *failed, size_t *resident_bytes, size_t *peak_resident_bytes);
+
+/* Cache counters since creation (each nullable): requests that found an
+ * idle entry with their trajectory (factors reused), requests that gave an
+ * idle entry of their shape a new trajectory in place, requests whose coil
+ * maps were already resident in their entry, and requests run by replaying
+ * their entry's captured graph. */
+MRI_API int mri_server_cache_stats(mri_server *server, uint64_t *plan_hits, uint64_t *plan_retargets,
+                                   uint64_t *maps_reused, uint64_t *graph_replays);
 
 /* Finish in-flight requests, fail the waiting ones, free everything.  No
  * other call on the server may be in progress or follow. */

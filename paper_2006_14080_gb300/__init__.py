@@ -116,6 +116,7 @@ def load(path: str = LIB_PATH):
         "mri_server_wait": ([P, ctypes.c_uint64, P, ctypes.POINTER(D), D], I),
         "mri_server_stats": ([P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(ctypes.c_uint64),
                               ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Z), ctypes.POINTER(Z)], I),
+        "mri_server_cache_stats": ([P] + [ctypes.POINTER(ctypes.c_uint64)] * 4, I),
         "mri_server_destroy": ([P], I),
         "mri_tuning_save": ([ctypes.c_char_p], I),
         "mri_tuning_load": ([ctypes.c_char_p], I),
@@ -482,8 +483,11 @@ class Server:
         res, peak = ctypes.c_size_t(), ctypes.c_size_t()
         _check(load().mri_server_stats(self._h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(done),
                                        ctypes.byref(failed), ctypes.byref(res), ctypes.byref(peak)))
+        c = [ctypes.c_uint64() for _ in range(4)]
+        _check(load().mri_server_cache_stats(self._h, *[ctypes.byref(q) for q in c]))
         return {"p50_ms": p50.value, "p99_ms": p99.value, "completed": done.value, "failed": failed.value,
-                "resident_bytes": res.value, "peak_resident_bytes": peak.value}
+                "resident_bytes": res.value, "peak_resident_bytes": peak.value, "plan_hits": c[0].value,
+                "plan_retargets": c[1].value, "maps_reused": c[2].value, "graph_replays": c[3].value}
 
     def close(self):
         if getattr(self, "_h", None) is not None:

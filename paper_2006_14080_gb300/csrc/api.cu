@@ -581,31 +581,33 @@ extern "C" {
 
 }  // extern "C"
 
-// mri_admm_reconstruct and mri_admm_resume: direct launches, or the cached
-// CUDA graph of the whole reconstruction while the arguments repeat.
-static int admm_run(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in, const mri_admm_params *prm,
-                    mri_c64 *image_out, double *objective_hist, double *alpha_hist, const AdmmWarm &warm,
-                    cudaStream_t s) {
+// mri_admm_reconstruct, mri_admm_resume and served requests: direct
+// launches, or the cached CUDA graph of the whole reconstruction while the
+// arguments repeat.
+int mri::run_admm(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_in, const mri_admm_params *prm,
+                  mri_c64 *image_out, double *objective_hist, double *alpha_hist, const AdmmWarm &warm,
+                  cudaStream_t s, bool coop) {
     const int arc = check_admm_args(p, kspace_in, maps_in, prm, image_out);
     if (arc != MRI_OK) return arc;
     // per-kernel timing events cannot be read back from graph replays, so a
     // timed plan launches its kernels directly
     if (!p->use_graphs || s == nullptr || p->timing)
-        return enqueue_admm(p, kspace_in, maps_in, prm, image_out, objective_hist, alpha_hist, s, warm);
+        return enqueue_admm(p, kspace_in, maps_in, prm, image_out, objective_hist, alpha_hist, s, warm, coop);
     const mri_plan::GraphKey key{kspace_in,  maps_in,   image_out,       objective_hist, alpha_hist,
                                  prm->lambda, prm->beta, prm->admm_iters, prm->cg_iters,  prm->rtol,
-                                 prm->atol,   warm.x0,   warm.eta0,       warm.eta_out};
+                                 prm->atol,   warm.x0,   warm.eta0,       warm.eta_out,   coop};
     if (p->graph_exec && p->graph_key == key) {
         cudaError_t e = cudaGraphLaunch(p->graph_exec, s);
         if (e != cudaSuccess) return cuda_fail(e, "graph launch");
         p->launches += p->graph_launches;
+        p->graph_replays += 1;
         return MRI_OK;
     }
     invalidate_graph(p);
     const long long l0 = p->launches;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "graph capture");
-    const int rc = enqueue_admm(p, kspace_in, maps_in, prm, image_out, objective_hist, alpha_hist, s, warm);
+    const int rc = enqueue_admm(p, kspace_in, maps_in, prm, image_out, objective_hist, alpha_hist, s, warm, coop);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(s, &graph);
     if (rc != MRI_OK || e != cudaSuccess) {
@@ -622,6 +624,7 @@ static int admm_run(mri_plan *p, const mri_c64 *kspace_in, const mri_c64 *maps_i
     }
     p->graph_key = key;
     p->graph_launches = p->launches - l0;
+    p->graph_captures += 1;
     e = cudaGraphLaunch(p->graph_exec, s);
     if (e != cudaSuccess) return cuda_fail(e, "graph launch");
     return MRI_OK;
@@ -633,7 +636,7 @@ MRI_API int mri_admm_reconstruct(mri_plan *p, const mri_c64 *kspace_in, const mr
                                  const mri_admm_params *prm, mri_c64 *image_out, double *objective_hist,
                                  double *alpha_hist, mri_stream_t stream) {
     NvtxRange range("mri_admm_reconstruct");
-    return admm_run(p, kspace_in, maps_in, prm, image_out, objective_hist, alpha_hist, AdmmWarm(),
+    return run_admm(p, kspace_in, maps_in, prm, image_out, objective_hist, alpha_hist, AdmmWarm(),
                     (cudaStream_t)stream);
 }
 
@@ -647,7 +650,7 @@ MRI_API int mri_admm_resume(mri_plan *p, const mri_c64 *kspace, const mri_c64 *m
     warm.eta_out = eta_out;
     if (eta_out && (eta_out == eta0 || (const void *)eta_out == (const void *)x0))
         return fail(MRI_ERR_INVALID, "eta_out must not alias x0 or eta0");
-    return admm_run(p, kspace, maps, prm, image_out, objective_hist, alpha_hist, warm, (cudaStream_t)stream);
+    return run_admm(p, kspace, maps, prm, image_out, objective_hist, alpha_hist, warm, (cudaStream_t)stream);
 }
 
 MRI_API int mri_plan_set_graphs(mri_plan *p, int enable) {

@@ -159,15 +159,17 @@ struct mri_plan {
         int admm_iters, cg_iters;
         double rtol, atol;
         const void *x0, *eta0, *eta_out;  // resumed reconstructions (else null)
+        bool coop;                         // CG step as one cooperative kernel, or as two kernels
         bool operator==(const GraphKey &o) const {
             return kspace == o.kspace && maps == o.maps && image_out == o.image_out && obj == o.obj &&
                    alpha == o.alpha && lambda == o.lambda && beta == o.beta && admm_iters == o.admm_iters &&
                    cg_iters == o.cg_iters && rtol == o.rtol && atol == o.atol && x0 == o.x0 && eta0 == o.eta0 &&
-                   eta_out == o.eta_out;
+                   eta_out == o.eta_out && coop == o.coop;
         }
     } graph_key{};
     cudaGraphExec_t graph_exec = nullptr;
     long long graph_launches = 0;  // kernels in one replay
+    long long graph_captures = 0, graph_replays = 0;  // reconstructions captured, and replayed from a graph
 };
 
 namespace mri {
@@ -201,6 +203,13 @@ struct AdmmWarm {
 int enqueue_admm(mri_plan *p, const mri_c64 *kspace, const mri_c64 *maps, const mri_admm_params *prm,
                  mri_c64 *image_out, double *objective_hist, double *alpha_hist, cudaStream_t s,
                  const AdmmWarm &warm = AdmmWarm(), bool coop = true);
+// enqueue_admm through the plan's cached CUDA graph of the whole
+// reconstruction: captured on the first call with these arguments (device
+// pointers, parameters, coop), replayed while they repeat; direct launches
+// when the plan's graphs are off, its timing is on, or s is the legacy stream.
+int run_admm(mri_plan *p, const mri_c64 *kspace, const mri_c64 *maps, const mri_admm_params *prm,
+             mri_c64 *image_out, double *objective_hist, double *alpha_hist, const AdmmWarm &warm, cudaStream_t s,
+             bool coop = true);
 }  // namespace mri
 
 // Record the timing events (when set) immediately around a product kernel.

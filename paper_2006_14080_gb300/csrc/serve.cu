@@ -6,13 +6,21 @@
 // admits the oldest pending request as soon as a stream slot is free and its
 // device memory fits the budget, so requests that arrive while others run
 // start as slots and memory free up and their kernels overlap on the GPU.
-// DFT factors are kept resident in a plan cache keyed by shape and trajectory
-// (idle plans are evicted least-recently-used when the budget needs room);
-// plans and per-request buffers come from a stream-ordered pool and are
-// freed stream-ordered, so no step of the loop, eviction included,
-// synchronises the device.  Each request is reconstructed by exactly
-// the kernels it would use alone (own plan, own workspace), so its result
-// does not depend on what else is in flight.
+// A cache of plan entries keeps DFT factors, coil maps and the request
+// buffers resident: an entry is a plan for one shape and trajectory (its
+// factors) plus fixed device buffers for k-space, coil maps and the image.
+// A request whose trajectory and coil maps equal an idle entry's (compared
+// byte for byte against host copies the entry keeps) uploads only its
+// k-space; from an entry's second request on, its reconstruction is a CUDA
+// graph captured once and replayed (the fixed buffers keep the launch
+// arguments the same).  Idle entries are evicted least-recently-used when
+// the budget needs room; an idle entry of the request's shape is given the
+// new trajectory in place when nothing else fits.  Entries and per-request
+// buffers come from a stream-ordered pool and are freed stream-ordered, so
+// no step of the loop, eviction included, synchronises the device.  Each
+// request is reconstructed by exactly the kernels it would use alone (own
+// plan, own workspace), so its result does not depend on what else is in
+// flight, nor on whether it ran from a graph.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -47,8 +55,11 @@ struct PlanEntry {
     mri_plan *plan = nullptr;
     bool busy = false;
     uint64_t last_use = 0;
-    size_t bytes = 0;
-    cudaStream_t last_stream = nullptr;  // stream of the plan's last work (stream-ordered free)
+    size_t bytes = 0;                    // the plan's device bytes plus the three buffers below
+    cudaStream_t last_stream = nullptr;  // stream of the entry's last work (stream-ordered free)
+    void *d_k = nullptr, *d_maps = nullptr, *d_img = nullptr;  // fixed request buffers
+    void *h_traj = nullptr, *h_maps = nullptr;  // pinned host copies of what the plan and d_maps hold
+    int uses = 0;                               // requests served
 };
 
 struct Job {
@@ -57,9 +68,10 @@ struct Job {
     uint64_t traj_hash = 0;
     size_t traj_bytes = 0, k_bytes = 0, maps_bytes = 0, img_bytes = 0;
     void *h_traj = nullptr, *h_k = nullptr, *h_maps = nullptr, *h_img = nullptr;  // pinned staging
-    void *d_traj = nullptr, *d_k = nullptr, *d_maps = nullptr, *d_img = nullptr;
-    size_t dev_bytes = 0;
+    void *d_traj = nullptr;  // device trajectory, only while the entry's factors are (re)generated
+    size_t dev_bytes = 0;    // transient device bytes of the request (its trajectory upload)
     PlanEntry *entry = nullptr;
+    bool hit = false;       // the entry already holds this trajectory's factors
     bool retarget = false;  // the entry is an idle plan of the same shape given this request's trajectory
     int slot = -1;
     cudaEvent_t done_ev = nullptr;
@@ -86,6 +98,7 @@ struct mri_server {
     std::multimap<size_t, void *> pinned_pool;  // free pinned staging buffers by size
     std::vector<double> latencies_ms;
     uint64_t next_ticket = 1, use_clock = 0, completed = 0, failed = 0;
+    uint64_t plan_hits = 0, plan_retargets = 0, maps_reused = 0, graph_replays = 0;
     bool stop = false;
     std::thread worker;
 };
@@ -115,7 +128,22 @@ void pinned_put(mri_server *s, void *p, size_t bytes) {
 size_t stage_img_bytes(const Job *j) { return j->img_bytes + 16; }
 int *job_status_word(Job *j) { return (int *)((char *)j->h_img + j->img_bytes); }
 
-size_t job_buffer_bytes(const Job *j) { return j->traj_bytes + j->k_bytes + j->maps_bytes + j->img_bytes; }
+// Device bytes of an entry's fixed request buffers (k-space, maps, image).
+size_t entry_buffer_bytes(const Job *j) { return j->k_bytes + j->maps_bytes + j->img_bytes; }
+
+// Frees an entry (no work of it pending on `st` beyond what is already
+// ordered there) and takes its bytes off the resident count.
+void drop_entry(mri_server *s, PlanEntry *pe, cudaStream_t st) {
+    if (pe->plan) mri::plan_destroy_async(pe->plan, st);
+    void *bufs[] = {pe->d_k, pe->d_maps, pe->d_img};
+    for (void *b : bufs)
+        if (b) cudaFreeAsync(b, st);
+    pinned_put(s, pe->h_traj, (size_t)pe->nk * 2 * sizeof(float));
+    pinned_put(s, pe->h_maps, (size_t)pe->nc * pe->nx * pe->ny * sizeof(mri_c64));
+    s->resident -= pe->bytes;
+    s->plans.erase(std::find(s->plans.begin(), s->plans.end(), pe));
+    delete pe;
+}
 
 void fail_job(mri_server *s, Job *j, int code, const std::string &msg) {
     j->state = Job::kFailed;
@@ -130,42 +158,65 @@ int start_job(mri_server *s, Job *j) {
     mri::NvtxRange range("mri_server_start_job");
     cudaStream_t st = s->streams[j->slot];
     const mri_server_request &r = j->req;
+    PlanEntry *pe = j->entry;
+    pe->last_stream = st;
     cudaError_t e = cudaSuccess;
-    void **bufs[] = {&j->d_traj, &j->d_k, &j->d_maps, &j->d_img};
-    size_t sizes[] = {j->traj_bytes, j->k_bytes, j->maps_bytes, j->img_bytes};
-    for (int q = 0; q < 4 && e == cudaSuccess; ++q) e = cudaMallocFromPoolAsync(bufs[q], sizes[q], s->pool, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(j->d_traj, j->h_traj, j->traj_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(j->d_k, j->h_k, j->k_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(j->d_maps, j->h_maps, j->maps_bytes, cudaMemcpyHostToDevice, st);
+    if (!pe->d_k) {  // a new entry: its fixed buffers
+        void **bufs[] = {&pe->d_k, &pe->d_maps, &pe->d_img};
+        size_t sizes[] = {j->k_bytes, j->maps_bytes, j->img_bytes};
+        for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaMallocFromPoolAsync(bufs[q], sizes[q], s->pool, st);
+    }
+    if (e == cudaSuccess && !j->hit) {
+        e = cudaMallocFromPoolAsync(&j->d_traj, j->traj_bytes, s->pool, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(j->d_traj, j->h_traj, j->traj_bytes, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pe->d_k, j->h_k, j->k_bytes, cudaMemcpyHostToDevice, st);
+    // coil maps: resident when they equal what the entry already holds
+    const bool maps_same = pe->h_maps && std::memcmp(pe->h_maps, j->h_maps, j->maps_bytes) == 0;
+    if (e == cudaSuccess && !maps_same) {
+        e = cudaMemcpyAsync(pe->d_maps, j->h_maps, j->maps_bytes, cudaMemcpyHostToDevice, st);
+        // the staging buffer becomes the entry's host copy; the entry's old
+        // copy (idle: its upload finished with the entry's last request)
+        // returns to the pool with the job
+        std::swap(pe->h_maps, j->h_maps);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return MRI_ERR_CUDA;
     }
-    PlanEntry *pe = j->entry;
-    pe->last_stream = st;
+    if (maps_same) s->maps_reused += 1;
     if (!pe->plan) {
         // plan buffers come from the server's pool, so that evicting the plan
         // later frees them stream-ordered instead of synchronising the device
         int rc = mri::plan_create(&pe->plan, r.nx, r.ny, r.nk, r.nc, (const float *)j->d_traj, s->precision, st, s->pool);
         if (rc != MRI_OK) return rc;
-        mri_plan_set_graphs(pe->plan, 0);  // a request's buffers are new each time: launch directly
-        pe->bytes = mri_plan_device_bytes(pe->plan);
+        mri_plan_set_graphs(pe->plan, 0);
+        std::swap(pe->h_traj, j->h_traj);
     } else if (j->retarget) {
-        // same shape, other trajectory: regenerate the factors in place (Alg. 1)
+        // same shape, other trajectory: regenerate the factors in place (Alg. 1);
+        // the plan's buffers, and so its captured graph, stay valid
         pe->traj_hash = 0;
         int rc = mri_plan_set_trajectory(pe->plan, (const float *)j->d_traj, st);
         if (rc != MRI_OK) return rc;
         pe->traj_hash = j->traj_hash;
+        std::swap(pe->h_traj, j->h_traj);
+        s->plan_retargets += 1;
+    } else {
+        s->plan_hits += 1;
     }
-    // requests run concurrently: CG steps as ordinary kernels (a cooperative
-    // grid would wait for the whole GPU), the same results as alone
-    int rc = mri::check_admm_args(pe->plan, (const mri_c64 *)j->d_k, (const mri_c64 *)j->d_maps, &r.params,
-                                  (const mri_c64 *)j->d_img);
-    if (rc == MRI_OK)
-        rc = mri::enqueue_admm(pe->plan, (const mri_c64 *)j->d_k, (const mri_c64 *)j->d_maps, &r.params,
-                               (mri_c64 *)j->d_img, nullptr, nullptr, st, mri::AdmmWarm(), false);
+    // from the entry's second request on, the whole reconstruction is a CUDA
+    // graph over the entry's fixed buffers: captured once, then replayed.
+    // Requests run concurrently, so the CG steps are two ordinary kernels (a
+    // cooperative grid would wait for the whole GPU), with the same results
+    // as alone.
+    pe->uses += 1;
+    mri_plan_set_graphs(pe->plan, pe->uses >= 2);
+    const long long replays0 = pe->plan->graph_replays;
+    int rc = mri::run_admm(pe->plan, (const mri_c64 *)pe->d_k, (const mri_c64 *)pe->d_maps, &r.params,
+                           (mri_c64 *)pe->d_img, nullptr, nullptr, mri::AdmmWarm(), st, false);
     if (rc != MRI_OK) return rc;
-    e = cudaMemcpyAsync(j->h_img, j->d_img, j->img_bytes, cudaMemcpyDeviceToHost, st);
+    s->graph_replays += (uint64_t)(pe->plan->graph_replays - replays0);
+    e = cudaMemcpyAsync(j->h_img, pe->d_img, j->img_bytes, cudaMemcpyDeviceToHost, st);
     // the plan's deferred status word (bounded device waits) travels with the image
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(job_status_word(j), &pe->plan->scal->status, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -175,11 +226,10 @@ int start_job(mri_server *s, Job *j) {
 
 void release_job_device(mri_server *s, Job *j) {
     cudaStream_t st = s->streams[j->slot];
-    void *bufs[] = {j->d_traj, j->d_k, j->d_maps, j->d_img};
-    for (void *b : bufs)
-        if (b) cudaFreeAsync(b, st);
-    j->d_traj = j->d_k = j->d_maps = j->d_img = nullptr;
+    if (j->d_traj) cudaFreeAsync(j->d_traj, st);
+    j->d_traj = nullptr;
     s->resident -= j->dev_bytes;
+    j->dev_bytes = 0;
     s->slot_busy[j->slot] = false;
     if (j->entry) {
         j->entry->busy = false;
@@ -187,17 +237,14 @@ void release_job_device(mri_server *s, Job *j) {
     }
 }
 
-// Evict idle cached plans, least recently used first, until `need` more bytes fit.
+// Evict idle cached entries, least recently used first, until `need` more bytes fit.
 void make_room(mri_server *s, size_t need) {
     while (s->resident + need > s->budget) {
         PlanEntry *victim = nullptr;
         for (PlanEntry *pe : s->plans)
             if (!pe->busy && pe->plan && (!victim || pe->last_use < victim->last_use)) victim = pe;
         if (!victim) return;
-        s->resident -= victim->bytes;
-        mri::plan_destroy_async(victim->plan, victim->last_stream);  // idle: its last work has completed
-        s->plans.erase(std::find(s->plans.begin(), s->plans.end(), victim));
-        delete victim;
+        drop_entry(s, victim, victim->last_stream);  // idle: its last work has completed
     }
 }
 
@@ -250,38 +297,43 @@ void worker_loop(mri_server *s) {
             if (slot < 0) break;
             Job *j = s->pending.front();
             const mri_server_request &r = j->req;
-            // plan: an idle cached plan of this shape and trajectory; else a
-            // new one if it fits; else an idle plan of the same shape given
-            // this trajectory (no allocation); else a new one after evicting
+            // entry: an idle cached entry of this shape and trajectory (the
+            // trajectory compared byte for byte); else a new one if it fits;
+            // else an idle entry of the same shape given this trajectory in
+            // place (no allocation); else a new one after evicting
             PlanEntry *pe = nullptr, *same_shape = nullptr;
             for (PlanEntry *c : s->plans) {
                 if (c->busy || c->nx != r.nx || c->ny != r.ny || c->nk != r.nk || c->nc != r.nc || !c->plan) continue;
-                if (c->traj_hash == j->traj_hash) {
+                if (c->traj_hash == j->traj_hash && c->h_traj &&
+                    std::memcmp(c->h_traj, j->h_traj, j->traj_bytes) == 0) {
                     pe = c;
                     break;
                 }
                 if (!same_shape || c->last_use < same_shape->last_use) same_shape = c;
             }
-            size_t plan_bytes = pe ? 0 : mri_plan_estimate_bytes(r.nx, r.ny, r.nk, r.nc, s->precision);
-            size_t need = plan_bytes + job_buffer_bytes(j);
+            const size_t plan_est = pe ? 0 : mri_plan_estimate_bytes(r.nx, r.ny, r.nk, r.nc, s->precision);
+            size_t entry_bytes = pe ? 0 : plan_est + entry_buffer_bytes(j);  // a new entry's resident bytes
+            const size_t transient = pe ? 0 : j->traj_bytes;  // the trajectory upload for its factors
+            size_t need = entry_bytes + transient;
+            j->hit = pe != nullptr;
             j->retarget = false;
             if (!pe && same_shape && s->resident + need > s->budget) {
                 pe = same_shape;
                 j->retarget = true;
-                plan_bytes = 0;
-                need = job_buffer_bytes(j);
+                entry_bytes = 0;
+                need = transient;
             }
-            if ((!pe && plan_bytes == 0) || need > s->budget) {
+            if ((!pe && plan_est == 0) || need > s->budget) {
                 s->pending.pop_front();
                 fail_job(s, j, MRI_ERR_NOMEM,
-                         plan_bytes == 0 && !pe ? "request shape not supported"
-                                                : "request needs " + std::to_string(need) +
-                                                      " bytes, more than the whole budget");
+                         plan_est == 0 && !pe ? "request shape not supported"
+                                              : "request needs " + std::to_string(need) +
+                                                    " bytes, more than the whole budget");
                 s->cv_done.notify_all();
                 continue;
             }
             if (s->resident + need > s->budget) {
-                if (pe) pe->busy = true;  // keep the matching plan out of the eviction
+                if (pe) pe->busy = true;  // keep the matching entry out of the eviction
                 make_room(s, need);
                 if (pe) pe->busy = false;
             }
@@ -289,33 +341,29 @@ void worker_loop(mri_server *s) {
             s->pending.pop_front();
             if (!pe) {
                 pe = new PlanEntry{r.nx, r.ny, r.nk, r.nc, j->traj_hash};
-                pe->bytes = plan_bytes;
+                pe->bytes = entry_bytes;
                 s->plans.push_back(pe);
             }
             pe->busy = true;
             j->entry = pe;
             j->slot = slot;
-            j->dev_bytes = job_buffer_bytes(j) + plan_bytes;  // the plan's bytes move to the cache on release
+            j->dev_bytes = transient;  // the entry's bytes stay resident with the cache
             s->slot_busy[slot] = true;
             s->resident += need;
             s->peak_resident = std::max(s->peak_resident, s->resident);
             j->state = Job::kRunning;
             const int rc = start_job(s, j);
-            if (plan_bytes) {
-                // the plan stays resident after the job; account it to the cache
-                j->dev_bytes -= plan_bytes;
-                if (pe->plan) {
-                    s->resident += pe->bytes - plan_bytes;  // actual instead of estimate
-                    s->peak_resident = std::max(s->peak_resident, s->resident);
-                }
+            if (entry_bytes && pe->plan) {  // the plan's actual bytes instead of the estimate
+                const size_t actual = mri_plan_device_bytes(pe->plan) + entry_buffer_bytes(j);
+                s->resident = s->resident - pe->bytes + actual;
+                pe->bytes = actual;
+                s->peak_resident = std::max(s->peak_resident, s->resident);
             }
             if (rc != MRI_OK) {
                 fail_job(s, j, rc, mri_last_error());
                 release_job_device(s, j);
                 if (!pe->plan) {
-                    s->resident -= pe->bytes;
-                    s->plans.erase(std::find(s->plans.begin(), s->plans.end(), pe));
-                    delete pe;
+                    drop_entry(s, pe, s->streams[slot]);
                     j->entry = nullptr;
                 }
                 s->cv_done.notify_all();
@@ -487,6 +535,17 @@ MRI_API int mri_server_stats(mri_server *s, double *p50_ms, double *p99_ms, uint
     return MRI_OK;
 }
 
+MRI_API int mri_server_cache_stats(mri_server *s, uint64_t *plan_hits, uint64_t *plan_retargets,
+                                   uint64_t *maps_reused, uint64_t *graph_replays) {
+    if (!s) return set_error("null server"), MRI_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (plan_hits) *plan_hits = s->plan_hits;
+    if (plan_retargets) *plan_retargets = s->plan_retargets;
+    if (maps_reused) *maps_reused = s->maps_reused;
+    if (graph_replays) *graph_replays = s->graph_replays;
+    return MRI_OK;
+}
+
 MRI_API int mri_server_destroy(mri_server *s) {
     if (!s) return MRI_OK;
     {
@@ -510,6 +569,11 @@ MRI_API int mri_server_destroy(mri_server *s) {
     }
     for (PlanEntry *pe : s->plans) {
         if (pe->plan) mri_plan_destroy(pe->plan);
+        void *bufs[] = {pe->d_k, pe->d_maps, pe->d_img};
+        for (void *b : bufs)
+            if (b) cudaFree(b);
+        if (pe->h_traj) cudaFreeHost(pe->h_traj);
+        if (pe->h_maps) cudaFreeHost(pe->h_maps);
         delete pe;
     }
     for (auto &kv : s->pinned_pool) cudaFreeHost(kv.second);

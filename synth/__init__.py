@@ -242,6 +242,24 @@ def batch_item(j: int) -> Problem:
                    noise, 0.005, 1e-3, 1.0, 30, 8, 4000 + j)
 
 
+def batch_item_shape(j: int):
+    """(N, coils, spokes) of batch item ``j``: the first three draws of its
+    generator, without building its phantom, maps or noise."""
+    rng = np.random.default_rng(4000 + j)
+    n = int(rng.choice([64, 128, 192, 256]))
+    nc = int(rng.choice([8, 16, 32]))
+    return n, nc, int(rng.integers(32, 201))
+
+
+# A stratified subsample of the 64 batch items: two of each image size, all
+# three coil counts present (item: N, coils, spokes -- 59: 64, 32, 40;
+# 62: 64, 16, 57; 11: 128, 8, 77; 46: 128, 16, 120; 16: 192, 8, 52;
+# 34: 192, 8, 58; 36: 256, 8, 35; 17: 256, 8, 52), within each stratum the
+# items with the fewest samples, so that the FP64 oracle reconstructs all
+# eight at the full 30 x 8 steps in a few CPU-hours.
+BATCH_SUBSAMPLE = (59, 62, 11, 46, 16, 34, 36, 17)
+
+
 def serve_request(r: int) -> Problem:
     """Request ``r`` of the serving stream: sizes drawn as for the batch items
     (N in {64,128,192,256}, coils in {8,16,32}, 32..200 golden-angle spokes of

@@ -6,7 +6,7 @@ and relative-change histories, and fingerprints of the k-space input (its
 L2 norm and a few samples) so that a consumer can confirm it regenerated the
 same measurement.
 
-    python tests/golden/make_golden.py small medium large3x3
+    python tests/golden/make_golden.py small medium large3x3 batch_subsample
 """
 import os
 import sys
@@ -30,7 +30,14 @@ def config_large_3x3():
     return p
 
 
-CONFIGS = {"small": synth.config_small, "medium": synth.config_medium, "large3x3": config_large_3x3}
+def batch_subsample():
+    """The stratified subsample of the 64-item heterogeneous batch, at the
+    batch's own 30 ADMM x 8 CG steps (one file per item)."""
+    return [synth.batch_item(j) for j in synth.BATCH_SUBSAMPLE]
+
+
+CONFIGS = {"small": synth.config_small, "medium": synth.config_medium, "large3x3": config_large_3x3,
+           "batch_subsample": batch_subsample}
 SAMPLE_IDX = np.array([0, 1, 17, 1000, 4093, 16383, 123456, 196607])
 
 
@@ -41,16 +48,19 @@ def fingerprint(d):
 
 
 def main(names):
+    problems = []
     for name in names:
-        p = CONFIGS[name]()
+        got = CONFIGS[name]()
+        problems.extend(got if isinstance(got, list) else [got])
+    for p in problems:
         t0 = time.time()
         d = oracle.measurements(p)
         out = oracle.admm(p.traj, p.maps, d, p.lam, p.beta, p.admm_iters, p.cg_iters)
         norm, idx, samples = fingerprint(d)
         path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"admm_{p.name}.npz")
-        # the N=256 image is stored in complex64 (relative rounding 6e-8, far below
-        # the 1e-3 image bar) to keep the file small
-        x = out["x"].astype(np.complex64) if p.nx >= 256 else out["x"]
+        # images of N=256 and of the batch items are stored in complex64
+        # (relative rounding 6e-8, far below the 1e-3 image bar) to keep the files small
+        x = out["x"].astype(np.complex64) if (p.nx >= 256 or p.name.startswith("batch")) else out["x"]
         np.savez_compressed(path, x=x, objective=out["objective"], alpha=out["alpha"],
                             d_norm=norm, d_idx=idx, d_samples=samples,
                             lam=p.lam, beta=p.beta, admm_iters=p.admm_iters, cg_iters=p.cg_iters)

@@ -5,6 +5,8 @@ reconstructed alone: the batch only changes when kernels run, never which
 kernels, tiles or summation orders compute a request.  One request is the
 N=32 workload, checked against the FP64 oracle as in test_gpu_admm.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -13,6 +15,8 @@ import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 @pytest.fixture(scope="module")
@@ -88,3 +92,104 @@ def test_batch_rejects_shared_plans(mr):
             batch.reconstruct([dict(it, out=torch.empty((p.nx, p.ny), dtype=torch.complex64, device="cuda")),
                                dict(it, out=torch.empty((p.nx, p.ny), dtype=torch.complex64, device="cuda"))])
         assert ei.value.code == mr.MRI_ERR_INVALID
+
+
+def _golden_item(p):
+    path = os.path.join(GOLDEN, f"admm_{p.name}.npz")
+    return np.load(path) if os.path.exists(path) else None
+
+
+def _subsample_data(p):
+    # the oracle's seeded measurement, as the stored oracle image was made from
+    return oracle.measurements(p)
+
+
+@pytest.mark.slow
+def test_batch64_equals_alone_and_subsample_operators_match_oracle(mr):
+    """The 64-item heterogeneous batch at its real sizes and counts (N in
+    {64,128,192,256}, 8-32 coils, 32-200 spokes of 2N samples, 30 ADMM x 8 CG,
+    BF16x3): every item of the batch equals its alone-run image bit for bit,
+    and on the stratified subsample (two items per image size, every coil
+    count) the forward and adjoint operators of each item's plan match the
+    FP64 oracle at sampled outputs within the 1e-5 operator bar.  Items
+    outside the subsample reconstruct seeded synthetic k-space (the oracle's
+    measurement of 56 more items would take CPU-hours); the equality check
+    needs no particular data."""
+    sub = set(synth.BATCH_SUBSAMPLE)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        probs, items, plans, data = [], [], [], {}
+        for j in range(64):
+            p = synth.batch_item(j)
+            d = _subsample_data(p) if j in sub else (0.05 * p.noise).astype(np.complex64)
+            data[j] = d
+            plan = mr.Plan(p.nx, p.ny, p.nc, _dev(p.traj, torch.float32), "bf16x3")
+            probs.append(p)
+            plans.append(plan)
+            items.append({"plan": plan, "kspace": _dev(d), "coil_maps": _dev(p.maps),
+                          "out": torch.full((p.nx, p.ny), float("nan"), dtype=torch.complex64, device="cuda"),
+                          "lam": p.lam, "beta": p.beta, "admm_iters": p.admm_iters, "cg_iters": p.cg_iters})
+        with mr.Batch() as batch:
+            batch.reconstruct(items)
+            batched = [it["out"].cpu().numpy() for it in items]
+        alone = [mr.admm_reconstruct(it["plan"], it["kspace"], it["coil_maps"], it["lam"], it["beta"],
+                                     it["admm_iters"], it["cg_iters"]).cpu().numpy() for it in items]
+        ops = {}
+        rng = np.random.default_rng(64)
+        for j in sorted(sub):
+            p, it = probs[j], items[j]
+            x = synth.random_complex(rng, (p.nx, p.ny))
+            ks = np.sort(rng.choice(p.nk, size=min(p.nk, 384), replace=False))
+            px = np.sort(rng.choice(p.nx * p.ny, size=48, replace=False))  # flat pixel indices i*ny + j
+            fwd = mr.nudft_forward(it["plan"], _dev(x), it["coil_maps"]).cpu().numpy()[:, ks]
+            adj = mr.nudft_adjoint(it["plan"], it["kspace"], it["coil_maps"]).cpu().numpy().reshape(-1)[px]
+            ops[j] = (x, ks, px, fwd, adj)
+        for plan in plans:
+            plan.sync_status()
+            plan.close()
+    for a, b in zip(batched, alone):
+        assert np.all(np.isfinite(a)) and np.array_equal(a, b)
+    for j in sorted(sub):
+        p = probs[j]
+        x, ks, px, fwd, adj = ops[j]
+        ref_f = oracle.forward(p.traj[ks], x, p.maps)
+        ref_a = oracle.adjoint_at(p.traj, data[j], p.maps, px)
+        ef = np.linalg.norm(fwd - ref_f) / np.linalg.norm(ref_f)
+        ea = np.linalg.norm(adj - ref_a) / np.linalg.norm(ref_a)
+        print(f"{p.name}: forward {ef:.2e}, adjoint {ea:.2e} at sampled outputs")
+        assert ef <= 1e-5 and ea <= 1e-5, p.name
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["bf16x3", "fp32"])
+def test_batch_subsample_images_match_oracle(mr, precision):
+    """The stratified subsample of the 64-item batch, reconstructed as one
+    batch at the full 30 ADMM x 8 CG steps, against the FP64 oracle's images
+    of the same seeded measurements (tests/golden, written by make_golden.py
+    from the oracle alone): NRMSE <= 1e-3 for every item in both forms."""
+    probs = [synth.batch_item(j) for j in synth.BATCH_SUBSAMPLE]
+    goldens = [_golden_item(p) for p in probs]
+    if any(g is None for g in goldens):
+        pytest.skip("stored oracle images of the batch subsample missing (make_golden.py batch_subsample)")
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        items, plans = [], []
+        for p, g in zip(probs, goldens):
+            d = _subsample_data(p)
+            assert abs(np.linalg.norm(d.astype(np.complex128)) - float(g["d_norm"])) <= 1e-9 * float(g["d_norm"])
+            plan = mr.Plan(p.nx, p.ny, p.nc, _dev(p.traj, torch.float32), precision)
+            plans.append(plan)
+            items.append({"plan": plan, "kspace": _dev(d), "coil_maps": _dev(p.maps),
+                          "out": torch.full((p.nx, p.ny), float("nan"), dtype=torch.complex64, device="cuda"),
+                          "lam": p.lam, "beta": p.beta, "admm_iters": p.admm_iters, "cg_iters": p.cg_iters})
+        with mr.Batch() as batch:
+            batch.reconstruct(items)
+            got = [it["out"].cpu().numpy() for it in items]
+        for plan in plans:
+            plan.sync_status()
+            plan.close()
+    for p, g, x in zip(probs, goldens, got):
+        ref = g["x"].astype(np.complex128)
+        err = np.linalg.norm(x - ref) / np.linalg.norm(ref)
+        print(f"{p.name} {precision}: NRMSE vs FP64 oracle = {err:.3e}")
+        assert err <= 1e-3, p.name

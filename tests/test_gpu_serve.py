@@ -164,3 +164,35 @@ def test_serve_retargets_idle_plan_of_same_shape(mr):
     for a, b in zip(tight, alone):
         assert np.all(np.isfinite(a)) and np.array_equal(a, b)
     assert not np.array_equal(alone[0], alone[1])  # the trajectories do differ
+
+
+def test_serve_keeps_maps_resident_and_replays_graphs(mr):
+    # one scanner session: the same trajectory and coil maps for several
+    # frames, then new maps, then a new trajectory.  One slot, so that every
+    # request finds the previous one's entry idle.  The entry's factors are
+    # reused from the second request on, its maps while they repeat, and its
+    # reconstruction is captured as a graph at the second request and
+    # replayed from the third; every image equals the direct reconstruction
+    base = synth.make_problem("s48g", 48, 3, 12, 96, seed=7301, golden=True, noise_level=0.01,
+                              admm_iters=4, cg_iters=3)
+    rng = np.random.default_rng(7302)
+    frames = [synth.add_noise(oracle.forward(base.traj, base.image_true, base.maps), synth.unit_noise(rng, base.nc,
+                                                                                                      base.nk), 0.01)
+              for _ in range(3)]
+    maps2 = synth.coil_maps(rng, 48, 48, base.nc)
+    traj2 = synth.radial_trajectory(12, 96, golden=True, rotation=0.5)
+    reqs = [(base.traj, f, base.maps) for f in frames] + [(base.traj, frames[0], maps2), (traj2, frames[1], maps2)]
+    with mr.Server(8 << 30, max_inflight=1) as srv:
+        got = [srv.wait(srv.submit(t, d, m, base.lam, base.beta, base.admm_iters, base.cg_iters))[0]
+               for t, d, m in reqs]
+        st = srv.stats()
+    assert st["completed"] == 5 and st["failed"] == 0
+    assert st["plan_hits"] == 3          # requests 2-4 reuse the first entry's factors
+    assert st["maps_reused"] == 2        # requests 2 and 3
+    assert st["graph_replays"] == 2      # requests 3 and 4 (request 2 captured the graph)
+    assert st["plan_retargets"] == 0     # the budget leaves room for a second entry
+    for (t, d, m), img in zip(reqs, got):
+        p = synth.Problem(base.name, 48, 48, base.nc, 12, 96, t, base.image_true, m, base.noise, 0.01, base.lam,
+                          base.beta, base.admm_iters, base.cg_iters, base.seed)
+        assert np.all(np.isfinite(img)) and np.array_equal(img, _direct(mr, p, d, "bf16x3"))
+    assert not np.array_equal(got[0], got[1]) and not np.array_equal(got[0], got[3])
