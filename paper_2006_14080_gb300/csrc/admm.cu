@@ -103,6 +103,28 @@ __device__ __forceinline__ float2 axpy(Split s, float2 v, float2 acc) {
 // Callers loop over (coil, pixel) pairs e = c npix + n, one per thread, so
 // that every coil's map entries and operand words are read and written
 // coalesced and the coils proceed in parallel.
+__device__ __forceinline__ float2 map_at(const float2 *__restrict__ mapsT, int ldm, int ny, int c, size_t n, int nx) {
+    return mapsT[((size_t)c * ny + n / nx) * ldm + n % nx];
+}
+// ... with the map entry s = map_at(...) already loaded.
+template <int kMode>
+__device__ __forceinline__ void put_operand_w(const Operand &op, int c, size_t e, size_t n, int nx, float2 s, float2 v) {
+    const int i = (int)(n % nx), j = (int)(n / nx);
+    const float2 w = cmul(s, v);
+    if constexpr (kMode == kOpFp32) {
+        op.fp32[e] = w;
+    } else {
+        const size_t off = ((size_t)c * op.ny_pad + j) * op.kx2 + i;
+        if constexpr (kMode == kOpTf32) {
+            op.t32[off] = make_uint2(tc::tf32_bits(w.x), tc::tf32_bits(w.y));
+        } else {
+            uint32_t h, l;
+            split2(w.x, w.y, h, l);
+            op.hi[off] = h;
+            op.lo[off] = l;
+        }
+    }
+}
 template <int kMode>
 __device__ __forceinline__ void put_operand_one(const Operand &op, const float2 *__restrict__ mapsT, int ldm, int ny,
                                                 size_t e, int c, size_t n, int nx, float2 v) {
@@ -164,10 +186,13 @@ struct Ring {
 };
 
 // One unit of a block's sequence: group g (coils [g cs, g cs + cs)) of the
-// block's item number u / n_groups.  Thread 0 stages each coil's ksplit
-// contiguous 64-pixel partial rows and its 64 map entries with two bulk
-// copies completing on the stage's mbarrier.
+// block's item number u / n_groups.  Called by the lanes of warp 0: lane l
+// stages coil g cs + l -- its ksplit contiguous 64-pixel partial rows and its
+// 64 map entries, two bulk copies completing on the stage's mbarrier -- and
+// lane 0 also arrives with the unit's byte count (a copy may land before
+// that arrival: the phase completes only once both have happened).
 __device__ __forceinline__ void issue_unit(const Partials &P, const Ring &R, int u) {
+    const int lane = threadIdx.x & 31;
     const int k = u / P.n_groups, g = u - k * P.n_groups;
     const int item = blockIdx.x + k * gridDim.x;
     const int ig = item % P.n_ig, j = item / P.n_ig;
@@ -176,8 +201,8 @@ __device__ __forceinline__ void issue_unit(const Partials &P, const Ring &R, int
     float2 *stage = R.buf + (size_t)slot * R.stage_elems;
     const uint32_t bar = tc::smem_u32(R.full + slot);
     tc::fence_proxy_async_smem();  // the stage's previous contents were read through the generic proxy
-    tc::mbar_arrive_expect_tx(bar, (uint32_t)((c1 - c0) * P.chunk * sizeof(float2)));
-    for (int c = c0; c < c1; ++c) {
+    if (lane == 0) tc::mbar_arrive_expect_tx(bar, (uint32_t)((c1 - c0) * P.chunk * sizeof(float2)));
+    for (int c = c0 + lane; c < c1; c += 32) {
         float2 *dst = stage + (size_t)(c - c0) * P.chunk;
         const float2 *src = P.part + (((size_t)c * P.ny + j) * P.n_ig + ig) * P.ksplit * 64;
         tc::bulk_load(tc::smem_u32(dst), src, (uint32_t)(P.ksplit * 64 * sizeof(float2)), bar);
@@ -188,24 +213,32 @@ __device__ __forceinline__ void issue_unit(const Partials &P, const Ring &R, int
 
 // sum_c conj(S_c) sum_p part over the block's items (item = blockIdx.x +
 // k gridDim.x < n_items), staged through shared memory by TMA bulk copies
-// (two stages in flight).  Thread row ty sums coil g cs + ty of each stage
-// g for the lane's pixels 64 ig + 2 tx and + 1: its k-space splits in
-// increasing order (four interleaved chains) times conj(S_c), added to the
-// row's running value in increasing coil order; the rows are then added in
-// increasing order.  For each item, epi(item, j, ig, i, v) runs in thread
-// rows 0 and 1 (pixel i = 64 ig + 2 tx + ty, v its value; i may lie past
-// the image), then done(item) in every thread.  Returns false if a stage
-// wait ran out (kStatusTimeout is recorded).  All threads of the block must
-// call it.
+// (two stages in flight).  Every thread row takes part in each stage: the
+// rpc = 16 / cs rows of coil slot q = ty / rpc each add the k-space splits
+// p = s, s + rpc, s + 2 rpc, ... (s = ty % rpc, increasing order, two
+// interleaved chains) for the lane's pixels 64 ig + 2 tx and + 1; row q rpc
+// then adds the slot's rpc sums in pairs of increasing s, multiplies by conj(S_c)
+// and adds that to its running value (coils in increasing order); the rows
+// are finally added in increasing order.  The splits of a coil are summed
+// completely before the multiplication: partial images over subsets of the
+// splits are far larger than their sum (radial streaks that cancel), and a
+// product rounded per subset would carry that larger size into the error.
+// The order depends on the plan's shape only.  For each item, epi(item, j, ig,
+// i, v) runs in thread rows 0 and 1 (pixel i = 64 ig + 2 tx + ty, v its
+// value; i may lie past the image), then done(item) in every thread.
+// Returns false if a stage wait ran out (kStatusTimeout is recorded).  All
+// threads of the block must call it.
 template <typename Epi, typename Done>
 __device__ __forceinline__ bool staged_items(const Partials &P, const Ring &R, int n_items, int *status,
                                              float4 (*grp)[kRedThreadsX], Epi epi, Done done) {
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int my_items = n_items > (int)blockIdx.x ? (n_items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int units = my_items * P.n_groups;
-    int issued = 0;  // thread 0: units issued so far
-    if (flat_tid() == 0)
+    int issued = 0;  // warp 0: units issued so far
+    if (flat_tid() < 32)
         for (; issued < min(units, kRingStages); ++issued) issue_unit(P, R, issued);
+    // this row's coil slot and first split (rows past cs * rpc stay idle)
+    const int rpc = kRedGroups / P.cs, slot_q = ty / rpc, sub = ty - slot_q * rpc;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     bool ok = true;
     for (int u = 0; u < units; ++u) {
@@ -213,26 +246,34 @@ __device__ __forceinline__ bool staged_items(const Partials &P, const Ring &R, i
         const int slot = u % kRingStages;
         const uint32_t parity = (uint32_t)(u / kRingStages) & 1u;
         if (!tc::mbar_wait(tc::smem_u32(R.full + slot), parity, R.abort, kStageWaitNs)) ok = false;
-        const int c = g * P.cs + ty;
-        if (ok && ty < P.cs && c < P.nc) {
-            const float2 *chunk = R.buf + (size_t)slot * R.stage_elems + (size_t)ty * P.chunk;
+        const int c = g * P.cs + slot_q;
+        if (ok && slot_q < P.cs && c < P.nc) {
+            const float2 *chunk = R.buf + (size_t)slot * R.stage_elems + (size_t)slot_q * P.chunk;
             const float4 *src = reinterpret_cast<const float4 *>(chunk) + tx;  // 32 float4 per 64-pixel row
-            float4 w[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) w[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-            int p = 0;
-            for (; p + 3 < P.ksplit; p += 4)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) w[e] = f4add(w[e], src[(size_t)(p + e) * 32]);
-            for (; p < P.ksplit; ++p) w[p & 3] = f4add(w[p & 3], src[(size_t)p * 32]);
-            const float4 t = f4add(f4add(w[0], w[1]), f4add(w[2], w[3]));
+            float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f), w1 = w0;
+            int p = sub;
+            for (; p + rpc < P.ksplit; p += 2 * rpc) {
+                w0 = f4add(w0, src[(size_t)p * 32]);
+                w1 = f4add(w1, src[(size_t)(p + rpc) * 32]);
+            }
+            if (p < P.ksplit) w0 = f4add(w0, src[(size_t)p * 32]);
+            grp[ty][tx] = f4add(w0, w1);
+        }
+        __syncthreads();  // the slots' split sums are in grp
+        if (ok && sub == 0 && slot_q < P.cs && c < P.nc) {
+            const float2 *chunk = R.buf + (size_t)slot * R.stage_elems + (size_t)slot_q * P.chunk;
+            // pairs first: (t0 + t1) + (t2 + t3) + ..., a balanced tree for rpc = 2, 4
+            float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+            int q = 0;
+            for (; q + 1 < rpc; q += 2) t = f4add(t, f4add(grp[ty + q][tx], grp[ty + q + 1][tx]));
+            if (q < rpc) t = f4add(t, grp[ty + q][tx]);
             const float4 m = reinterpret_cast<const float4 *>(chunk + (size_t)P.ksplit * 64)[tx];
             const float2 a0 = cmulc(make_float2(m.x, m.y), make_float2(t.x, t.y));
             const float2 a1 = cmulc(make_float2(m.z, m.w), make_float2(t.z, t.w));
             acc = f4add(acc, make_float4(a0.x, a0.y, a1.x, a1.y));
         }
-        __syncthreads();  // the stage has been read
-        if (flat_tid() == 0 && ok && !*R.abort && u + kRingStages < units) issue_unit(P, R, issued++);
+        __syncthreads();  // the stage and grp have been read
+        if (flat_tid() < 32 && ok && !*R.abort && u + kRingStages < units) issue_unit(P, R, issued++);
         if (g == P.n_groups - 1) {
             const int item = blockIdx.x + k * gridDim.x;
             grp[ty][tx] = acc;
@@ -277,25 +318,26 @@ __device__ __forceinline__ Ring make_ring(const Partials &P, uint8_t *smem, vola
     return R;
 }
 
-// Bounded grid-wide barrier of a cooperative launch: bar[0] counts arrivals,
-// bar[1] is the generation.  Returns false (and records kStatusTimeout) if
-// the other blocks did not arrive within the limit.
+// Bounded grid-wide barrier of a cooperative launch.  bar[0] counts
+// arrivals and only grows (reset to 0 once per reconstruction, a multiple
+// of the grid size before every use): a block's ticket t names its barrier,
+// which is complete when the count reaches the next multiple of the grid
+// size past t.  Nobody resets anything, so the last block's arrival alone
+// releases the others.  Returns false (and records kStatusTimeout) if the
+// other blocks did not arrive within the limit.
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *status) {
     __shared__ int ok_s;
     __syncthreads();
     if (flat_tid() == 0) {
         int ok = 1;
-        volatile unsigned *vgen = bar + 1;
-        const unsigned gen = *vgen;
-        __threadfence();
         const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
-        if (atomicAdd(bar, 1u) == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
+        __threadfence();  // the block's writes (made visible to thread 0 by the barrier above) before the arrival
+        const unsigned ticket = atomicAdd(bar, 1u);
+        const unsigned target = ticket - ticket % nblocks + nblocks;
+        volatile unsigned *vbar = bar;
+        if ((int)(*vbar - target) < 0) {
             const uint64_t t0 = tc::global_timer_ns();
-            while (*vgen == gen) {
+            while ((int)(*vbar - target) < 0) {
                 if (tc::global_timer_ns() - t0 > kBarrierLimitNs) {
                     atomicExch(status, kStatusTimeout);
                     ok = 0;
@@ -369,8 +411,10 @@ struct CgArgs {
 // Re<r, A d> + alpha^2 ||A d||^2 (the square expanded, so that one
 // grid-wide reduction serves alpha and beta) and beta = tau' / tau, from the
 // per-item partial triples; out[0..2] = alpha, tau', beta in every thread.
+// rtau = 1 / tau, formed by the caller before the reduction (off the
+// critical path: beta = tau' rtau needs no division after it).
 __device__ __forceinline__ void cg_scalars(const double *partials, int n_items, double *stage, double tau,
-                                           double *out) {
+                                           double rtau, double *out) {
     double t3[3];
     sum_partials3(partials, n_items, stage, 2 * kMinStageElems, t3);
     if (flat_tid() == 0) {
@@ -378,7 +422,7 @@ __device__ __forceinline__ void cg_scalars(const double *partials, int n_items, 
         const double tau_next = tau - 2.0 * alpha * t3[1] + alpha * alpha * t3[2];
         out[0] = alpha;
         out[1] = tau_next;
-        out[2] = tau_next / tau;
+        out[2] = tau_next * rtau;
     }
     __syncthreads();
 }
@@ -396,7 +440,10 @@ __device__ __forceinline__ void cg_updates(const CgArgs &A, double alpha, double
     const size_t total = npix * A.P.nc;
     for (size_t e0 = gtid; e0 < total; e0 += 2 * gstride) {
         // two pairs e0 and e0 + gstride per pass, loads of both issued first
-        float2 rv[2], dv[2], adv[2];
+        // every load of both pairs (r, d, A d, the map entry and, for coil 0,
+        // x) is issued before the first store, so that one round trip to
+        // memory serves the pass
+        float2 rv[2], dv[2], adv[2], sv[2], xv[2];
         size_t n[2];
         int c[2];
 #pragma unroll
@@ -408,6 +455,8 @@ __device__ __forceinline__ void cg_updates(const CgArgs &A, double alpha, double
                 rv[h] = A.r[n[h]];
                 dv[h] = A.d[n[h]];
                 adv[h] = A.ad[n[h]];
+                sv[h] = map_at(A.P.mapsT, A.P.n_ig * 64, ny, c[h], n[h], nx);
+                if (c[h] == 0) xv[h] = A.x[n[h]];
             }
         }
 #pragma unroll
@@ -416,11 +465,11 @@ __device__ __forceinline__ void cg_updates(const CgArgs &A, double alpha, double
             const float2 rn = axpy(sna, adv[h], rv[h]);
             const float2 nd = axpy(sb, dv[h], rn);
             if (c[h] == 0) {  // x is read and written by this thread only
-                A.x[n[h]] = axpy(sa, dv[h], A.x[n[h]]);
+                A.x[n[h]] = axpy(sa, dv[h], xv[h]);
                 A.r_next[n[h]] = rn;
                 A.d_next[n[h]] = nd;
             }
-            put_operand_one<kMode>(A.op, A.P.mapsT, A.P.n_ig * 64, ny, e0 + h * gstride, c[h], n[h], nx, nd);
+            put_operand_w<kMode>(A.op, c[h], e0 + h * gstride, n[h], nx, sv[h], nd);
         }
     }
 }
@@ -438,12 +487,12 @@ __device__ __forceinline__ void cg_reduce_items(const CgArgs &A, const Ring &R, 
         A.P, R, A.n_items, &A.sc->status, grp,
         [&](int, int j, int, int i, float2 v) {
             if (i >= nx) return;
+            const size_t n = (size_t)j * nx + i;
+            const float2 dv = A.d[n], rv = A.r[n];  // loaded with the stencil's, before the store
             const float2 tt = theta_h_thetaT(A.d, i, j, nx, ny);
             v.x = fmaf(A.half_beta, tt.x, v.x);
             v.y = fmaf(A.half_beta, tt.y, v.y);
-            const size_t n = (size_t)j * nx + i;
             A.ad[n] = v;
-            const float2 dv = A.d[n], rv = A.r[n];
             v3[0] = (double)dv.x * (double)v.x + (double)dv.y * (double)v.y;
             v3[1] = (double)rv.x * (double)v.x + (double)rv.y * (double)v.y;
             v3[2] = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
@@ -483,11 +532,12 @@ __global__ void __launch_bounds__(kRedThreads, 2) cg_step_kernel(const CgArgs A)
     __shared__ double scal_s[3];
     __shared__ int abort_s;
     const double tau = A.sc->tau;
+    const double rtau = 1.0 / tau;
     const Ring R = make_ring(A.P, dyn_smem, &abort_s);
     cg_reduce_items<kMode>(A, R, grp, red3);
     if (!grid_barrier(A.bar, &A.sc->status)) return;
     // every block forms the same scalars (the ring now stages the partials)
-    cg_scalars(A.partials, A.n_items, reinterpret_cast<double *>(R.buf), tau, scal_s);
+    cg_scalars(A.partials, A.n_items, reinterpret_cast<double *>(R.buf), tau, rtau, scal_s);
     const double alpha = scal_s[0], tau_next = scal_s[1], beta = scal_s[2];
     cg_updates<kMode>(A, alpha, beta, (size_t)blockIdx.x * kRedThreads + flat_tid(), (size_t)gridDim.x * kRedThreads);
     if (blockIdx.x == 0 && flat_tid() == 0) {
@@ -510,10 +560,11 @@ __global__ void __launch_bounds__(kRedThreads, 2) cg_reduce_kernel(const CgArgs 
     __shared__ double scal_s[3];
     __shared__ int abort_s;
     const double tau = A.sc->tau;
+    const double rtau = 1.0 / tau;
     const Ring R = make_ring(A.P, dyn_smem, &abort_s);
     cg_reduce_items<kMode>(A, R, grp, red3);
     if (!last_block_arrives(&A.sc->counters[kCntDot])) return;
-    cg_scalars(A.partials, A.n_items, reinterpret_cast<double *>(R.buf), tau, scal_s);
+    cg_scalars(A.partials, A.n_items, reinterpret_cast<double *>(R.buf), tau, rtau, scal_s);
     if (flat_tid() == 0) {
         A.sc->alpha = scal_s[0];
         A.sc->tau_next = scal_s[1];
