@@ -412,17 +412,24 @@ struct CgArgs {
 // grid-wide reduction serves alpha and beta) and beta = tau' / tau, from the
 // per-item partial triples; out[0..2] = alpha, tau', beta in every thread.
 // rtau = 1 / tau, formed by the caller before the reduction (off the
-// critical path: beta = tau' rtau needs no division after it).
+// critical path: beta = tau' rtau needs no division after it).  splits[0..2]
+// receive alpha, -alpha and beta as FP32 pairs for the updates, formed once
+// here: converting them in every thread would keep the SM's few FP64 lanes
+// busy for microseconds.
 __device__ __forceinline__ void cg_scalars(const double *partials, int n_items, double *stage, double tau,
-                                           double rtau, double *out) {
+                                           double rtau, double *out, Split *splits) {
     double t3[3];
     sum_partials3(partials, n_items, stage, 2 * kMinStageElems, t3);
     if (flat_tid() == 0) {
         const double alpha = tau / t3[0];
         const double tau_next = tau - 2.0 * alpha * t3[1] + alpha * alpha * t3[2];
+        const double beta = tau_next * rtau;
         out[0] = alpha;
         out[1] = tau_next;
-        out[2] = tau_next * rtau;
+        out[2] = beta;
+        splits[0] = split_scalar(alpha);
+        splits[1] = split_scalar(-alpha);
+        splits[2] = split_scalar(beta);
     }
     __syncthreads();
 }
@@ -433,10 +440,10 @@ __device__ __forceinline__ void cg_scalars(const double *partials, int n_items, 
 // coil 0 stores x += alpha d, r' and d' (r' and d' into the other buffers:
 // r and d are still being read).
 template <int kMode>
-__device__ __forceinline__ void cg_updates(const CgArgs &A, double alpha, double beta, size_t gtid, size_t gstride) {
+__device__ __forceinline__ void cg_updates(const CgArgs &A, Split sa, Split sna, Split sb, size_t gtid,
+                                           size_t gstride) {
     const int nx = A.P.nx, ny = A.P.ny;
     const size_t npix = (size_t)nx * ny;
-    const Split sa = split_scalar(alpha), sna = split_scalar(-alpha), sb = split_scalar(beta);
     const size_t total = npix * A.P.nc;
     for (size_t e0 = gtid; e0 < total; e0 += 2 * gstride) {
         // two pairs e0 and e0 + gstride per pass, loads of both issued first
@@ -530,6 +537,7 @@ __global__ void __launch_bounds__(kRedThreads, 2) cg_step_kernel(const CgArgs A)
     __shared__ float4 grp[kRedGroups][kRedThreadsX];
     __shared__ double red3[3][2];
     __shared__ double scal_s[3];
+    __shared__ Split split_s[3];
     __shared__ int abort_s;
     const double tau = A.sc->tau;
     const double rtau = 1.0 / tau;
@@ -537,9 +545,10 @@ __global__ void __launch_bounds__(kRedThreads, 2) cg_step_kernel(const CgArgs A)
     cg_reduce_items<kMode>(A, R, grp, red3);
     if (!grid_barrier(A.bar, &A.sc->status)) return;
     // every block forms the same scalars (the ring now stages the partials)
-    cg_scalars(A.partials, A.n_items, reinterpret_cast<double *>(R.buf), tau, rtau, scal_s);
+    cg_scalars(A.partials, A.n_items, reinterpret_cast<double *>(R.buf), tau, rtau, scal_s, split_s);
     const double alpha = scal_s[0], tau_next = scal_s[1], beta = scal_s[2];
-    cg_updates<kMode>(A, alpha, beta, (size_t)blockIdx.x * kRedThreads + flat_tid(), (size_t)gridDim.x * kRedThreads);
+    cg_updates<kMode>(A, split_s[0], split_s[1], split_s[2], (size_t)blockIdx.x * kRedThreads + flat_tid(),
+                      (size_t)gridDim.x * kRedThreads);
     if (blockIdx.x == 0 && flat_tid() == 0) {
         A.sc->alpha = alpha;
         A.sc->beta_cg = beta;
@@ -558,17 +567,22 @@ __global__ void __launch_bounds__(kRedThreads, 2) cg_reduce_kernel(const CgArgs 
     __shared__ float4 grp[kRedGroups][kRedThreadsX];
     __shared__ double red3[3][2];
     __shared__ double scal_s[3];
+    __shared__ Split split_s[3];
     __shared__ int abort_s;
     const double tau = A.sc->tau;
     const double rtau = 1.0 / tau;
     const Ring R = make_ring(A.P, dyn_smem, &abort_s);
     cg_reduce_items<kMode>(A, R, grp, red3);
     if (!last_block_arrives(&A.sc->counters[kCntDot])) return;
-    cg_scalars(A.partials, A.n_items, reinterpret_cast<double *>(R.buf), tau, rtau, scal_s);
+    cg_scalars(A.partials, A.n_items, reinterpret_cast<double *>(R.buf), tau, rtau, scal_s, split_s);
     if (flat_tid() == 0) {
         A.sc->alpha = scal_s[0];
         A.sc->tau_next = scal_s[1];
         A.sc->beta_cg = scal_s[2];
+        for (int q = 0; q < 3; ++q) {
+            A.sc->cg_split[2 * q] = split_s[q].hi;
+            A.sc->cg_split[2 * q + 1] = split_s[q].lo;
+        }
         A.sc->step_pending = 1;
     }
 }
@@ -577,8 +591,9 @@ __global__ void __launch_bounds__(kRedThreads, 2) cg_reduce_kernel(const CgArgs 
 template <int kMode>
 __global__ void cg_update_kernel(const CgArgs A) {
     if (A.sc->admm_done || !A.sc->step_pending) return;
-    const double alpha = A.sc->alpha, beta = A.sc->beta_cg;
-    cg_updates<kMode>(A, alpha, beta, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
+    const float *f = A.sc->cg_split;  // alpha, -alpha, beta as FP32 pairs, formed once by the reduction
+    cg_updates<kMode>(A, Split{f[0], f[1]}, Split{f[2], f[3]}, Split{f[4], f[5]},
+                      (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
     if (!last_block_arrives(&A.sc->counters[kCntTau])) return;
     if (threadIdx.x == 0) {
         const double tau_next = A.sc->tau_next;

@@ -33,6 +33,7 @@ struct DevScalars {
     int step_active;    // the current ADMM step runs (ADMM had not stopped when it began)
     double tau_next;    // two-kernel CG step: ||r'||^2, handed from the reduction to the update
     int step_pending;   // two-kernel CG step: the reduction ran and its update is due
+    float cg_split[6];  // two-kernel CG step: alpha, -alpha, beta as FP32 (hi, lo) pairs
     unsigned counters[8];  // grid-reduction tickets, one per reduction site
 };
 
