@@ -48,9 +48,9 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # sources as captured: a changed kernel reports traffic null until it is
 # captured again.
 NCU_TRAFFIC = {
-    ("adj_tc_kernel", "n128_c12_s64x256"): (40.57e6, "c4f865303c5ac601", "profiles/adj_tc_kernel_n128.md"),
-    ("fwd_tc_kernel", "n128_c12_s64x256"): (52.05e6, "c4f865303c5ac601", "profiles/fwd_tc_kernel_n128.md"),
-    ("adj_tc_kernel", "n256_c32_s128x512"): (1302.56e6, "c4f865303c5ac601", "profiles/adj_tc_kernel_n256.md"),
+    ("adj_tc_kernel", "n128_c12_s64x256"): (40.44e6, "4e07d50614bdf6d9", "profiles/adj_tc_kernel_n128.md"),
+    ("fwd_tc_kernel", "n128_c12_s64x256"): (51.99e6, "4e07d50614bdf6d9", "profiles/fwd_tc_kernel_n128.md"),
+    ("adj_tc_kernel", "n256_c32_s128x512"): (1303.54e6, "4e07d50614bdf6d9", "profiles/adj_tc_kernel_n256.md"),
 }
 TC_SOURCES = ("nudft_tc.cu", "tc_ptx.cuh")
 
