@@ -161,6 +161,18 @@ def useful_flops_per_product(p):
     return 8.0 * p.nk * p.nx * p.ny * p.nc
 
 
+def cg_step_bytes(p, ksplit):
+    """Algorithmic bytes of one CG-step launch (BF16x3 form): reads of the
+    partial images (ksplit per coil, rows padded to 64 pixels), the coil maps
+    and d, r, x; writes of A d, x, r', d' and the next forward operand (BF16
+    hi + lo per coil and pixel)."""
+    nx_pad = -(-p.nx // 64) * 64
+    npix = p.nx * p.ny
+    reads = 8.0 * (ksplit * p.nc * nx_pad * p.ny + p.nc * nx_pad * p.ny + 3 * npix)
+    writes = 8.0 * (4 * npix + p.nc * npix)
+    return reads + writes
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -428,6 +440,8 @@ def run_gpu(args, rank, world, local_rank):
         normal_ops_per_recon(p) * 2 * flops_prod / (total_ms / args.steps * 1e-3) / 1e12
     dom_kernel = "adj_tc_kernel" if dom == "adj" else "fwd_tc_kernel"
     traffic, traffic_src = captured_traffic(dom_kernel, p.name)
+    red_avg = timing["red_ms"] / max(1, timing["red_launches"])
+    red_bytes = cg_step_bytes(p, (tuned or {}).get("adj_ksplit", 0) or 0)
     nrmse_vs_golden = None
     gpath = os.path.join(ROOT, "tests", "golden", f"admm_{p.name}.npz")
     if os.path.exists(gpath) and kspace_is_oracle(kspace_np, gpath):
@@ -468,8 +482,14 @@ def run_gpu(args, rank, world, local_rank):
                   "fwd_useful_tflops": flops_prod / (fwd_avg * 1e-3) / 1e12,
                   "adj_useful_tflops": flops_prod / (adj_avg * 1e-3) / 1e12,
                   "product_share_of_step": (timing["fwd_ms"] + timing["adj_ms"]) / kernel_pass_ms,
-                  "reduce_ms_per_launch": timing["red_ms"] / max(1, timing["red_launches"]),
+                  "reduce_ms_per_launch": red_avg,
                   "reduce_share_of_step": timing["red_ms"] / kernel_pass_ms,
+                  "reduce_bytes_per_launch": red_bytes,
+                  "reduce_gbs": red_bytes / (red_avg * 1e-3) / 1e9 if red_avg > 0 else None,
+                  "reduce_note": "the CG-step kernel: algorithmic bytes (partial images, maps, state, next forward "
+                                 "operand) per launch / mean event-timed launch; served mostly from L2 (the "
+                                 "partial images stay there between the adjoint and this kernel), so the HBM copy "
+                                 "peak bounds it only loosely",
                   "direct_launch_ms_per_step": kernel_pass_ms / len(ktimes),
                   "recon_useful_tflops": useful_tflops_step},
         "fp32_form": {"value": whole_job_rate(fp32_steps, t32_ms, world), "unit": "recon/s",
