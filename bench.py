@@ -859,7 +859,9 @@ def serve_measure(args, mr, dev, n_requests, rates, precisions, waves, warmup):
                               "wall_s": total_s})
             st = srv.stats()
         results[prec] = {"burst_capacity_recon_s": capacity, "capacity_requests": len(cap_items),
-                         "sweep": sweep, "peak_resident_bytes": st["peak_resident_bytes"]}
+                         "sweep": sweep, "peak_resident_bytes": st["peak_resident_bytes"],
+                         "cache": {k: st[k] for k in ("plan_hits", "plan_retargets", "maps_reused",
+                                                      "graph_replays")}}
     return results
 
 

@@ -245,9 +245,9 @@ MRI_API long long mri_batch_launch_count(const mri_batch *batch);
  * k-space, coil maps and image, which stay resident between requests.  A
  * request whose trajectory equals an idle entry's (byte for byte) reuses
  * the entry's factors; if its coil maps also equal the entry's, they are
- * not uploaded again.  From an entry's second request on, the
- * reconstruction runs as a CUDA graph captured once over the entry's
- * buffers and then replayed.  The scheduler starts the oldest waiting
+ * not uploaded again.  From the first request that finds an entry holding
+ * its trajectory, the entry's reconstruction runs as a CUDA graph captured
+ * once over its buffers and then replayed.  The scheduler starts the oldest waiting
  * request (first in, first out) as soon as a stream is free and its device
  * bytes -- a new entry's (mri_plan_estimate_bytes plus the three buffers)
  * and the trajectory upload, or nothing beyond the trajectory upload for a

@@ -11,8 +11,8 @@
 // factors) plus fixed device buffers for k-space, coil maps and the image.
 // A request whose trajectory and coil maps equal an idle entry's (compared
 // byte for byte against host copies the entry keeps) uploads only its
-// k-space; from an entry's second request on, its reconstruction is a CUDA
-// graph captured once and replayed (the fixed buffers keep the launch
+// k-space; from the first such request on, the entry's reconstruction is a
+// CUDA graph captured once and replayed (the fixed buffers keep the launch
 // arguments the same).  Idle entries are evicted least-recently-used when
 // the budget needs room; an idle entry of the request's shape is given the
 // new trajectory in place when nothing else fits.  Entries and per-request
@@ -58,8 +58,10 @@ struct PlanEntry {
     size_t bytes = 0;                    // the plan's device bytes plus the three buffers below
     cudaStream_t last_stream = nullptr;  // stream of the entry's last work (stream-ordered free)
     void *d_k = nullptr, *d_maps = nullptr, *d_img = nullptr;  // fixed request buffers
-    void *h_traj = nullptr, *h_maps = nullptr;  // pinned host copies of what the plan and d_maps hold
-    int uses = 0;                               // requests served
+    // host copies (ordinary memory) of the trajectory the plan's factors hold
+    // and of the maps d_maps holds, compared byte for byte with a request's
+    std::vector<uint8_t> h_traj, h_maps;
+    int hits = 0;  // requests that found this entry holding their trajectory
 };
 
 struct Job {
@@ -138,8 +140,6 @@ void drop_entry(mri_server *s, PlanEntry *pe, cudaStream_t st) {
     void *bufs[] = {pe->d_k, pe->d_maps, pe->d_img};
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, st);
-    pinned_put(s, pe->h_traj, (size_t)pe->nk * 2 * sizeof(float));
-    pinned_put(s, pe->h_maps, (size_t)pe->nc * pe->nx * pe->ny * sizeof(mri_c64));
     s->resident -= pe->bytes;
     s->plans.erase(std::find(s->plans.begin(), s->plans.end(), pe));
     delete pe;
@@ -172,13 +172,12 @@ int start_job(mri_server *s, Job *j) {
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(pe->d_k, j->h_k, j->k_bytes, cudaMemcpyHostToDevice, st);
     // coil maps: resident when they equal what the entry already holds
-    const bool maps_same = pe->h_maps && std::memcmp(pe->h_maps, j->h_maps, j->maps_bytes) == 0;
+    const bool maps_same = pe->h_maps.size() == j->maps_bytes &&
+                           std::memcmp(pe->h_maps.data(), j->h_maps, j->maps_bytes) == 0;
     if (e == cudaSuccess && !maps_same) {
         e = cudaMemcpyAsync(pe->d_maps, j->h_maps, j->maps_bytes, cudaMemcpyHostToDevice, st);
-        // the staging buffer becomes the entry's host copy; the entry's old
-        // copy (idle: its upload finished with the entry's last request)
-        // returns to the pool with the job
-        std::swap(pe->h_maps, j->h_maps);
+        const uint8_t *m = (const uint8_t *)j->h_maps;
+        pe->h_maps.assign(m, m + j->maps_bytes);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -191,7 +190,8 @@ int start_job(mri_server *s, Job *j) {
         int rc = mri::plan_create(&pe->plan, r.nx, r.ny, r.nk, r.nc, (const float *)j->d_traj, s->precision, st, s->pool);
         if (rc != MRI_OK) return rc;
         mri_plan_set_graphs(pe->plan, 0);
-        std::swap(pe->h_traj, j->h_traj);
+        const uint8_t *t = (const uint8_t *)j->h_traj;
+        pe->h_traj.assign(t, t + j->traj_bytes);
     } else if (j->retarget) {
         // same shape, other trajectory: regenerate the factors in place (Alg. 1);
         // the plan's buffers, and so its captured graph, stay valid
@@ -199,18 +199,21 @@ int start_job(mri_server *s, Job *j) {
         int rc = mri_plan_set_trajectory(pe->plan, (const float *)j->d_traj, st);
         if (rc != MRI_OK) return rc;
         pe->traj_hash = j->traj_hash;
-        std::swap(pe->h_traj, j->h_traj);
+        const uint8_t *t = (const uint8_t *)j->h_traj;
+        pe->h_traj.assign(t, t + j->traj_bytes);
         s->plan_retargets += 1;
     } else {
         s->plan_hits += 1;
     }
-    // from the entry's second request on, the whole reconstruction is a CUDA
-    // graph over the entry's fixed buffers: captured once, then replayed.
-    // Requests run concurrently, so the CG steps are two ordinary kernels (a
-    // cooperative grid would wait for the whole GPU), with the same results
-    // as alone.
-    pe->uses += 1;
-    mri_plan_set_graphs(pe->plan, pe->uses >= 2);
+    // from the first request that finds the entry holding its trajectory,
+    // the whole reconstruction is a CUDA graph over the entry's fixed
+    // buffers: captured once, then replayed (a new trajectory regenerated in
+    // place keeps it valid).  Entries that never see their trajectory again
+    // launch directly and pay no capture.  Requests run concurrently, so the
+    // CG steps are two ordinary kernels (a cooperative grid would wait for the
+    // whole GPU), with the same results as alone.
+    if (j->hit) pe->hits += 1;
+    mri_plan_set_graphs(pe->plan, pe->hits >= 1);
     const long long replays0 = pe->plan->graph_replays;
     int rc = mri::run_admm(pe->plan, (const mri_c64 *)pe->d_k, (const mri_c64 *)pe->d_maps, &r.params,
                            (mri_c64 *)pe->d_img, nullptr, nullptr, mri::AdmmWarm(), st, false);
@@ -304,8 +307,8 @@ void worker_loop(mri_server *s) {
             PlanEntry *pe = nullptr, *same_shape = nullptr;
             for (PlanEntry *c : s->plans) {
                 if (c->busy || c->nx != r.nx || c->ny != r.ny || c->nk != r.nk || c->nc != r.nc || !c->plan) continue;
-                if (c->traj_hash == j->traj_hash && c->h_traj &&
-                    std::memcmp(c->h_traj, j->h_traj, j->traj_bytes) == 0) {
+                if (c->traj_hash == j->traj_hash && c->h_traj.size() == j->traj_bytes &&
+                    std::memcmp(c->h_traj.data(), j->h_traj, j->traj_bytes) == 0) {
                     pe = c;
                     break;
                 }
@@ -572,8 +575,6 @@ MRI_API int mri_server_destroy(mri_server *s) {
         void *bufs[] = {pe->d_k, pe->d_maps, pe->d_img};
         for (void *b : bufs)
             if (b) cudaFree(b);
-        if (pe->h_traj) cudaFreeHost(pe->h_traj);
-        if (pe->h_maps) cudaFreeHost(pe->h_maps);
         delete pe;
     }
     for (auto &kv : s->pinned_pool) cudaFreeHost(kv.second);
