@@ -255,8 +255,9 @@ def batch_item_shape(j: int):
 # three coil counts present (item: N, coils, spokes -- 59: 64, 32, 40;
 # 62: 64, 16, 57; 11: 128, 8, 77; 46: 128, 16, 120; 16: 192, 8, 52;
 # 34: 192, 8, 58; 36: 256, 8, 35; 17: 256, 8, 52), within each stratum the
-# items with the fewest samples, so that the FP64 oracle reconstructs all
-# eight at the full 30 x 8 steps in a few CPU-hours.
+# items with the fewest samples (at N=128 the second is the fewest with 16
+# coils, so that every coil count is present), so that the FP64 oracle
+# reconstructs all eight at the full 30 x 8 steps in a few CPU-hours.
 BATCH_SUBSAMPLE = (59, 62, 11, 46, 16, 34, 36, 17)
 
 
