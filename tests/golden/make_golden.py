@@ -7,6 +7,7 @@ L2 norm and a few samples) so that a consumer can confirm it regenerated the
 same measurement.
 
     python tests/golden/make_golden.py small medium large3x3 batch_subsample
+    python tests/golden/make_golden.py --missing batch_subsample   # only images not stored yet
 """
 import os
 import sys
@@ -47,17 +48,19 @@ def fingerprint(d):
     return float(np.linalg.norm(flat.astype(np.complex128))), idx, flat[idx]
 
 
-def main(names):
+def main(names, missing_only=False):
     problems = []
     for name in names:
         got = CONFIGS[name]()
         problems.extend(got if isinstance(got, list) else [got])
     for p in problems:
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"admm_{p.name}.npz")
+        if missing_only and os.path.exists(path):
+            continue
         t0 = time.time()
         d = oracle.measurements(p)
         out = oracle.admm(p.traj, p.maps, d, p.lam, p.beta, p.admm_iters, p.cg_iters)
         norm, idx, samples = fingerprint(d)
-        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"admm_{p.name}.npz")
         # images of N=256 and of the batch items are stored in complex64
         # (relative rounding 6e-8, far below the 1e-3 image bar) to keep the files small
         x = out["x"].astype(np.complex64) if (p.nx >= 256 or p.name.startswith("batch")) else out["x"]
@@ -68,4 +71,7 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["small"])
+    args = sys.argv[1:]
+    missing = "--missing" in args
+    args = [a for a in args if a != "--missing"]
+    main(args or ["small"], missing_only=missing)
