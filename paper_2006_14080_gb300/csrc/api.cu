@@ -91,16 +91,29 @@ void free_plan(mri_plan *p, cudaStream_t free_stream = nullptr) {
 // alongside others).
 int choose_ksplit_fp32(const mri_plan *p, int *samples_per_split) {
     const int tiles = ceil_div(p->nx, 64) * ceil_div(p->ny, 64) * p->nc;
-    const int target = 2 * p->num_sms;
-    int split = std::max(1, std::min(ceil_div(target, tiles), ceil_div(p->nk, 256)));
-    // at most 4096 samples summed in one FP32 run: rounding error of a
-    // sequential FP32 sum of L random-phase terms grows like 2^-24 sqrt(L)
-    split = std::max(split, ceil_div(p->nk, 4096));
-    split = std::min(split, 64);
-    int per = round_up(ceil_div(p->nk, split), 16);
-    split = ceil_div(p->nk, per);
+    const int slots = adj_fp32_slots(p->num_sms);
+    // at most 4096 samples summed in one FP32 run (rounding error of a
+    // sequential FP32 sum of L random-phase terms grows like 2^-24 sqrt(L)),
+    // at least 256 (or the whole trajectory) per split, at most 64 splits;
+    // among those, the split count whose blocks take the fewest sample
+    // sweeps in waves of `slots` blocks (makespan = waves x samples per
+    // split), the smallest count on ties
+    const int lo = std::min(64, std::max(1, ceil_div(p->nk, 4096)));
+    const int hi = std::max(lo, std::min(64, ceil_div(p->nk, 256)));
+    long best_cost = -1;
+    int best = lo;
+    for (int split = lo; split <= hi; ++split) {
+        const int per = round_up(ceil_div(p->nk, split), 16);
+        const int eff = ceil_div(p->nk, per);
+        const long cost = (long)ceil_div(tiles * eff, slots) * per;
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = eff;
+        }
+    }
+    const int per = round_up(ceil_div(p->nk, best), 16);
     *samples_per_split = per;
-    return split;
+    return ceil_div(p->nk, per);
 }
 
 bool finite(float v) { return isfinite(v) != 0; }

@@ -234,6 +234,8 @@ cudaError_t launch_factors(mri_plan *p, const float *traj, cudaStream_t s);
 cudaError_t launch_fwd_fp32(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace, int ld,
                             int skip, cudaStream_t s);
 cudaError_t launch_adj_fp32(mri_plan *p, int skip, cudaStream_t s);
+// Blocks of the FP32 adjoint the GPU holds at once (its occupancy x num_sms).
+int adj_fp32_slots(int num_sms);
 
 // nudft_tc.cu -- same conventions (image == nullptr: the operand is already
 // in bfwd_hi/lo or bfwd_t, written by the solver)

@@ -67,15 +67,29 @@ __global__ void __launch_bounds__(256) fwd_fp32_kernel(const float2 *__restrict_
 
         // staging: A tile 64 rows x 16 cols, each thread 4 consecutive i of one row
         const int a_row = tid >> 2, a_col = (tid & 3) * 4;
-        // B tile 16 rows x 64 cols, each thread 4 consecutive j of one row
-        const int b_row = tid >> 4, b_col = (tid & 15) * 4;
+        // B tile 16 rows (i) x 64 cols (j), each thread 4 elements contiguous
+        // in memory: 4 consecutive j of one i (image layout [i][j]) or 4
+        // consecutive i of one j (the solver's transposed layout [j][i])
+        const int b_row = b_transposed ? (tid & 3) * 4 : tid >> 4;
+        const int b_col = b_transposed ? tid >> 2 : (tid & 15) * 4;
         float2 ra[4], rb[4];
         auto load = [&](int i0) {
+            const int kk = k0 + a_row, ii0 = i0 + a_col;
+            if (kk < nk && ii0 + 3 < nx && (nx & 1) == 0) {  // two aligned 16-byte loads
+                const float4 *src = reinterpret_cast<const float4 *>(ax + (size_t)kk * nx + ii0);
+                const float4 u = src[0], v = src[1];
+                ra[0] = make_float2(u.x, u.y);
+                ra[1] = make_float2(u.z, u.w);
+                ra[2] = make_float2(v.x, v.y);
+                ra[3] = make_float2(v.z, v.w);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    ra[q] = (kk < nk && ii0 + q < nx) ? ax[(size_t)kk * nx + ii0 + q] : make_float2(0.f, 0.f);
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int kk = k0 + a_row, ii = i0 + a_col + q;
-                ra[q] = (kk < nk && ii < nx) ? ax[(size_t)kk * nx + ii] : make_float2(0.f, 0.f);
-                const int bi = i0 + b_row, bj = j0 + b_col + q;
+                const int bi = i0 + b_row + (b_transposed ? q : 0), bj = j0 + b_col + (b_transposed ? 0 : q);
                 rb[q] = (bi < nx && bj < ny) ? B[b_transposed ? (size_t)bj * nx + bi : (size_t)bi * ny + bj]
                                              : make_float2(0.f, 0.f);
             }
@@ -84,7 +98,10 @@ __global__ void __launch_bounds__(256) fwd_fp32_kernel(const float2 *__restrict_
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 As[buf][a_col + q][a_row] = ra[q];
-                Bs[buf][b_row][b_col + q] = rb[q];
+                if (b_transposed)
+                    Bs[buf][b_row + q][b_col] = rb[q];
+                else
+                    Bs[buf][b_row][b_col + q] = rb[q];
             }
         };
         load(0);
@@ -260,6 +277,17 @@ __global__ void __launch_bounds__(256) adj_fp32_kernel(const float2 *__restrict_
 }
 
 }  // namespace
+
+// Blocks of the FP32 adjoint that the GPU holds at once (occupancy x SMs).
+int adj_fp32_slots(int num_sms) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_fp32_kernel, 256, 0) != cudaSuccess ||
+        per_sm <= 0) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm * num_sms;
+}
 
 cudaError_t launch_fwd_fp32(mri_plan *p, const float2 *image, const float2 *maps, float2 *kspace, int ld,
                             int skip, cudaStream_t s) {

@@ -150,11 +150,13 @@ def test_degenerate_shapes(mr, precision):
         assert _rel(adj, oracle.adjoint(traj, y, maps)) <= OP_TOL[precision]
 
 
-def test_tile_configurations_change_schedule_not_results(mr):
+@pytest.mark.parametrize("shape", [(128, 128, 12), (192, 160, 6)])
+def test_tile_configurations_change_schedule_not_results(mr, shape):
     # coils per forward tile and the stage counts of both operand rings change
     # the schedule only; every valid configuration must give bit-identical
-    # products (same arithmetic, same order)
-    nx, ny, nc = 128, 128, 12
+    # products (same arithmetic, same order), in the pixel-row adjoint tiles
+    # (128 x 128) and the row-pair ones (192 x 160)
+    nx, ny, nc = shape
     maps, traj, x, y = _case(nx, ny, nc, 24, 256, seed=31)
     with mr.Plan(nx, ny, nc, _dev(traj, torch.float32), "bf16x3") as plan:
         dm, dx, dy = _dev(maps), _dev(x), _dev(y)
@@ -172,7 +174,9 @@ def test_tile_configurations_change_schedule_not_results(mr):
                 if ref_f is None:
                     ref_f, ref_a = f, a
                 assert np.array_equal(f, ref_f) and np.array_equal(a, ref_a), (cpt, fs, ast)
-        assert len({t[0] for t in tried}) >= 2 and len(tried) >= 4
+        assert len(tried) >= 2
+        if ny <= 128:  # two coils fit one 256-column tile
+            assert len({t[0] for t in tried}) >= 2 and len(tried) >= 4
         with pytest.raises(mr.MriError):
             plan.set_tiles(5, 2, 2)
         cfg = plan.autotune(repeats=2)
@@ -183,17 +187,19 @@ def test_tile_configurations_change_schedule_not_results(mr):
     assert _rel(ref_a, oracle.adjoint(traj, y, maps)) <= OP_TOL["bf16x3"]
 
 
+@pytest.mark.parametrize("shape", [(128, 128, 12, 64, 256), (192, 160, 6, 40, 384)])
 @pytest.mark.parametrize("precision", ["bf16x3", "tf32", "fp32"])
-def test_repeated_calls_and_plans_are_bit_identical(mr, precision):
+def test_repeated_calls_and_plans_are_bit_identical(mr, precision, shape):
     # every operator sums in a fixed order, so repeating a call, or making it
     # on a second plan of the same shape, must give the same bits.  The
     # 128 x 128 image with 12 coils and 16,384 samples takes the pixel-row
     # adjoint with a dozen or more K splits per coil: the shape on which a
     # producer warp that reached its .sync.aligned TMEM stores diverged left
     # some lanes' operand rows late and changed the TF32 adjoint from call
-    # to call (up to 3.6e-3 relative, rows 0-31 only)
-    nx, ny, nc = 128, 128, 12
-    maps, traj, x, y = _case(nx, ny, nc, 64, 256, seed=41)
+    # to call (up to 3.6e-3 relative, rows 0-31 only).  The 192 x 160 image
+    # takes the row-pair adjoint tiles instead.
+    nx, ny, nc, spokes, readout = shape
+    maps, traj, x, y = _case(nx, ny, nc, spokes, readout, seed=41)
     dm, dx, dy, dt = _dev(maps), _dev(x), _dev(y), _dev(traj, torch.float32)
     runs = []
     for _ in range(2):
