@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 import torch
 
+import fp32_floor
 import oracle
 import synth
 
@@ -67,15 +68,20 @@ def test_paper_128x64_table1_matches_oracle(mr, small, precision):
     # This is the workload on which the paper measured its FP32-vs-FP64 ADMM
     # difference, about 1% (Section V).  With lambda = 1e-7 it is barely
     # regularised, 8x undersampled and solved 20 CG steps deep, so rounding
-    # anywhere is amplified: a CPU restatement of the FP64 solver with the
-    # oracle's own operators and only its vector sums reordered lands 2.5e-4
-    # from the oracle, and storing the vectors in FP32 (FP64 step lengths,
-    # exact operators) 3.3e-3.  The 1e-3 target is out of reach for any form
-    # with FP32 vectors here; the paper's 1% is the bar.  TF32 is not
-    # FP32-equivalent (10-bit operand mantissas, ~80x the FP32 form's operator
-    # error); it is held to the paper's 5%, the typical error of a
-    # compressed-sensing reconstruction itself (Section V).
-    assert err <= (5e-2 if precision == "tf32" else 1e-2)
+    # anywhere is amplified: storing the iterates in FP32 with exact operators
+    # (fp32_floor.py) lands 3.7e-3 from the oracle, so the 1e-3 target is out
+    # of reach for any form with FP32 vectors here.  The FP32 and BF16x3 forms
+    # are held to twice that floor (fp32_floor.image_bar), inside the paper's
+    # 1%.  TF32 is not FP32-equivalent (10-bit operand mantissas, ~80x the
+    # FP32 form's operator error); it is held to the paper's 5%, the typical
+    # error of a compressed-sensing reconstruction itself (Section V).
+    if precision == "tf32":
+        bar = 5e-2
+    else:
+        floor = fp32_floor.nrmse(fp32_floor.reconstruct(p, d, True, rtol=p.rtol, atol=p.atol)[0], ref["x"])
+        bar = fp32_floor.image_bar(floor)
+        print(f"paper 128x64: FP32-storage floor {floor:.3e}, bar {bar:.3e}")
+    assert err <= bar
 
 
 @pytest.fixture(scope="module")
