@@ -175,9 +175,10 @@ int start_job(mri_server *s, Job *j) {
     const bool maps_same = pe->h_maps.size() == j->maps_bytes &&
                            std::memcmp(pe->h_maps.data(), j->h_maps, j->maps_bytes) == 0;
     if (e == cudaSuccess && !maps_same) {
+        pe->h_maps.clear();  // the entry's maps are unknown until the copy is queued
         e = cudaMemcpyAsync(pe->d_maps, j->h_maps, j->maps_bytes, cudaMemcpyHostToDevice, st);
         const uint8_t *m = (const uint8_t *)j->h_maps;
-        pe->h_maps.assign(m, m + j->maps_bytes);
+        if (e == cudaSuccess) pe->h_maps.assign(m, m + j->maps_bytes);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -363,12 +364,13 @@ void worker_loop(mri_server *s) {
                 s->peak_resident = std::max(s->peak_resident, s->resident);
             }
             if (rc != MRI_OK) {
+                // a start that failed part-way leaves the entry's factors, maps
+                // or graph in an unknown state: it leaves the cache (its frees
+                // are ordered after whatever the slot's stream already holds)
                 fail_job(s, j, rc, mri_last_error());
                 release_job_device(s, j);
-                if (!pe->plan) {
-                    drop_entry(s, pe, s->streams[slot]);
-                    j->entry = nullptr;
-                }
+                drop_entry(s, pe, s->streams[slot]);
+                j->entry = nullptr;
                 s->cv_done.notify_all();
                 continue;
             }
