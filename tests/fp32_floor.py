@@ -80,6 +80,41 @@ class NormalOperator:
         return np.sum(self.maps.conj() * v, axis=0) + 0.5 * self.beta * _tv_adjoint(_tv_forward(p))
 
 
+class FP32Operator:
+    """Eq. 11 with the DFT products in single precision: the separable
+    factors A_x, A_y (Eq. 1-2, phases reduced in FP64) rounded to complex64
+    and the per-coil products y_c = rowsum((A_x (S_c x)) * A_y) and
+    x = sum_c conj(S_c) (A_x^H diag(y_c) conj(A_y)) taken as complex64
+    matrix products with FP32 accumulation.  It stands for any FP32
+    implementation of the operators, not for one kernel's summation order."""
+
+    def __init__(self, traj, maps, beta):
+        nc, nx, ny = maps.shape
+        traj = np.asarray(traj, np.float64)
+
+        def factor(k, n):
+            t = np.outer(k, np.arange(n, dtype=np.float64) - n // 2)
+            return np.exp(-2j * np.pi * (t - np.rint(t))).astype(np.complex64)
+
+        self.ax = factor(traj[:, 0], nx)  # nk x nx
+        ay = factor(traj[:, 1], ny)  # nk x ny
+        self.ay_t = np.ascontiguousarray(ay.T)
+        self.ay_conj = np.ascontiguousarray(ay.conj())
+        self.ax_conj_t = np.ascontiguousarray(self.ax.conj().T)
+        self.maps = np.asarray(maps, np.complex64)
+        self.half_beta = np.complex64(0.5 * beta)
+
+    def __call__(self, p):
+        nc, nx, ny = self.maps.shape
+        q = np.asarray(p, np.complex64)
+        g = (self.maps * q).reshape(nc * nx, ny) @ self.ay_t  # (c, i) x kappa
+        y = np.einsum("cik,ki->ck", g.reshape(nc, nx, -1), self.ax)
+        w = (y[:, None, :] * self.ax_conj_t[None]).reshape(nc * nx, -1)
+        xc = (w @ self.ay_conj).reshape(nc, nx, ny)
+        out = np.sum(self.maps.conj() * xc, axis=0) + self.half_beta * _tv_adjoint(_tv_forward(q))
+        return out.astype(np.complex128)
+
+
 def _store64(a):
     return a
 
@@ -88,14 +123,16 @@ def _store32(a):
     return a.astype(np.complex64).astype(np.complex128)
 
 
-def reconstruct(problem, kspace, fp32_storage, rtol=0.0, atol=0.0):
+def reconstruct(problem, kspace, fp32_storage, rtol=0.0, atol=0.0, fp32_operators=False):
     """Alg. 4 for ``problem`` (a synth.Problem) on the measurement ``kspace``,
-    with every stored vector rounded to complex64 when ``fp32_storage``.  The
+    with every stored vector rounded to complex64 when ``fp32_storage``, and
+    the normal operator taken in single precision (FP32Operator) when
+    ``fp32_operators``.  The
     outer loop stops once the relative change ||x' - x||^2 / ||x'||^2 is at
     most rtol^2, each CG once ||r||^2 is at most atol^2, as in the oracle.
     Returns the image and the number of outer steps taken."""
     store = _store32 if fp32_storage else _store64
-    op = NormalOperator(problem.traj, problem.maps, problem.beta)
+    op = (FP32Operator if fp32_operators else NormalOperator)(problem.traj, problem.maps, problem.beta)
     lam, beta = problem.lam, problem.beta
     fhd = store(oracle.adjoint(problem.traj, kspace, problem.maps))
     x = np.zeros(fhd.shape, np.complex128)

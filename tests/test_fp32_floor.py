@@ -67,3 +67,16 @@ def test_fp32_storage_floor_paper_128x64():
     floor = fp32_floor.nrmse(x32, ref["x"])
     print(f"{p.name}: FP32-storage floor {floor:.3e} after {steps32} steps")
     assert steps32 == ref["steps"] and floor > 1e-3
+
+
+def test_fp32_operators_add_to_the_storage_floor_within_the_target():
+    """On the N=32 workload: the storage floor, then FP32 operators on top of
+    it (complex64 products with FP32 accumulation), both within 1e-3."""
+    p = synth.config_small()
+    g = np.load(os.path.join(GOLDEN, f"admm_{p.name}.npz"))
+    d = oracle.measurements(p)
+    assert abs(np.linalg.norm(d.astype(np.complex128)) - float(g["d_norm"])) <= 1e-9 * float(g["d_norm"])
+    floor = fp32_floor.nrmse(fp32_floor.reconstruct(p, d, True)[0], g["x"])
+    ops = fp32_floor.nrmse(fp32_floor.reconstruct(p, d, True, fp32_operators=True)[0], g["x"])
+    print(f"{p.name}: FP32 storage {floor:.3e}, FP32 storage and operators {ops:.3e}")
+    assert floor < ops <= 1e-3
