@@ -1,6 +1,7 @@
 // C-ABI entry points of libmrirecon: argument checks, plan and workspace
 // management, and the host-side sequencing of the reconstruction (Alg. 4 with
 // Alg. 2 inside), all enqueued on the caller's stream without synchronising.
+#include <atomic>
 #include <math.h>
 #include <stdio.h>
 
@@ -17,6 +18,7 @@ static thread_local std::string g_last_error;
 void set_error(const std::string &msg) { g_last_error = msg; }
 
 void invalidate_graph(mri_plan *p) {
+    p->config_gen += 1;
     if (p->graph_exec) {
         cudaGraphExecDestroy(p->graph_exec);
         p->graph_exec = nullptr;
@@ -243,7 +245,9 @@ int plan_create(mri_plan **out, int nx, int ny, int nk, int nc, const float *tra
     if (precision != MRI_FP32 && !is_tc_precision(precision)) return fail(MRI_ERR_INVALID, "unknown precision");
     cudaStream_t s = (cudaStream_t)stream;
 
+    static std::atomic<uint64_t> next_serial{1};
     mri_plan *p = new mri_plan();
+    p->serial = next_serial.fetch_add(1);
     p->pool = pool;
     p->pool_stream = s;
     p->nx = nx;

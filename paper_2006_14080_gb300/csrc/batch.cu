@@ -3,7 +3,8 @@
 // factors, tiles and workspace) is captured into a child graph; the children
 // are independent nodes of one parent graph, so the GPU runs them
 // concurrently and one cudaGraphLaunch replays the whole batch.  The parent
-// graph is cached while the requests (plans, pointers, parameters) repeat.
+// graph is cached while the requests (plans, pointers, parameters) repeat and
+// each plan is the same plan (serial) in the same configuration (generation).
 // A request's result does not depend on the others: every request is
 // computed by exactly the kernels, tiles and summation order it would use
 // alone.
@@ -15,6 +16,7 @@
 
 struct mri_batch {
     std::vector<mri_request> key;
+    std::vector<std::pair<uint64_t, uint64_t>> plan_ids;  // (serial, config_gen) of each request's plan
     cudaGraphExec_t exec = nullptr;
     cudaStream_t capture = nullptr;
     long long launches = 0;  // kernels in one replay
@@ -39,6 +41,7 @@ void drop(mri_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
     b->key.clear();
+    b->plan_ids.clear();
     b->launches = 0;
 }
 
@@ -87,7 +90,9 @@ MRI_API int mri_batch_reconstruct(mri_batch *b, int n, const mri_request *reqs, 
     }
     cudaStream_t s = (cudaStream_t)stream;
     bool hit = b->exec && (int)b->key.size() == n;
-    for (int q = 0; hit && q < n; ++q) hit = same_request(b->key[q], reqs[q]);
+    for (int q = 0; hit && q < n; ++q)
+        hit = same_request(b->key[q], reqs[q]) &&
+              b->plan_ids[q] == std::make_pair(reqs[q].plan->serial, reqs[q].plan->config_gen);
     if (!hit) {
         drop(b);
         cudaGraph_t parent = nullptr;
@@ -122,6 +127,8 @@ MRI_API int mri_batch_reconstruct(mri_batch *b, int n, const mri_request *reqs, 
             return fail(MRI_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
         }
         b->key.assign(reqs, reqs + n);
+        b->plan_ids.clear();
+        for (int q = 0; q < n; ++q) b->plan_ids.emplace_back(reqs[q].plan->serial, reqs[q].plan->config_gen);
         b->launches = launches;
     }
     cudaError_t e = cudaGraphLaunch(b->exec, s);

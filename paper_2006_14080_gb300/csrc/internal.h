@@ -171,6 +171,12 @@ struct mri_plan {
     cudaGraphExec_t graph_exec = nullptr;
     long long graph_launches = 0;  // kernels in one replay
     long long graph_captures = 0, graph_replays = 0;  // reconstructions captured, and replayed from a graph
+    // Identity for graphs captured outside the plan (batches): unique per plan
+    // in the process, so that a new plan at a freed plan's address never
+    // matches, and a generation that grows whenever the plan's own graph is
+    // dropped because its captured arguments went stale.
+    uint64_t serial = 0;
+    uint64_t config_gen = 0;
 };
 
 namespace mri {

@@ -95,6 +95,38 @@ def test_batch_rejects_shared_plans(mr):
         assert ei.value.code == mr.MRI_ERR_INVALID
 
 
+def test_batch_cache_does_not_outlive_its_plans(mr):
+    """One batch reused across plans that were closed and created again, with
+    the same k-space, maps and output tensors: the new plans may come back at
+    the old plans' addresses, but the cached launch is keyed on each plan's
+    identity and configuration, so every result equals the new plan's alone
+    run, bit for bit."""
+    probs = _problems()[:2]
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side), mr.Batch() as batch:
+        data = [(_dev(oracle.measurements(p)), _dev(p.maps)) for p in probs]
+        outs = [torch.empty((p.nx, p.ny), dtype=torch.complex64, device="cuda") for p in probs]
+        captures = []
+        for _ in range(3):
+            plans = [mr.Plan(p.nx, p.ny, p.nc, _dev(p.traj, torch.float32), "fp32") for p in probs]
+            items = [{"plan": pl, "kspace": k, "coil_maps": m, "out": o, "lam": p.lam, "beta": p.beta,
+                      "admm_iters": p.admm_iters, "cg_iters": p.cg_iters}
+                     for p, pl, (k, m), o in zip(probs, plans, data, outs)]
+            for o in outs:
+                o.fill_(float("nan"))
+            batch.reconstruct(items)
+            got = [o.cpu().numpy() for o in outs]
+            for it, x in zip(items, got):
+                alone = mr.admm_reconstruct(it["plan"], it["kspace"], it["coil_maps"], it["lam"], it["beta"],
+                                            it["admm_iters"], it["cg_iters"]).cpu().numpy()
+                assert np.all(np.isfinite(x)) and np.array_equal(x, alone)
+            captures.append(batch.launch_count())
+            for pl in plans:
+                pl.sync_status()
+                pl.close()
+        assert all(c > 0 for c in captures)
+
+
 def _golden_item(p):
     path = os.path.join(GOLDEN, f"admm_{p.name}.npz")
     return np.load(path) if os.path.exists(path) else None
